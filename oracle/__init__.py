@@ -1,0 +1,259 @@
+"""CPU oracle for the segmented-range hot path (arXiv 2406.00158).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the benchmark's CPU-baseline / reference leg, never by the product path.
+It shares no code with the CUDA library.
+
+The heavy functions are plain sequential C++ (``dr_oracle.cpp``) loaded with
+ctypes; the zip re-segmentation oracle is a brute-force Python loop over
+element ownership (small inputs only).  Each function cites the passage it
+follows; see ``dr_oracle.cpp`` for the arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dr_oracle.cpp")
+_LIB = os.path.join(_HERE, "libdr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_SIGS = {
+    "oracle_inclusive_scan_i64": (None, [_P, _I64, _P]),
+    "oracle_inclusive_scan_f32_f64": (None, [_P, _I64, _P, _P]),
+    "oracle_inclusive_scan_f64": (None, [_P, _I64, _P]),
+    "oracle_inclusive_scan_f32_seq": (None, [_P, _I64, _P]),
+    "oracle_segmented_scan_alg4_i64": (None, [ctypes.c_int, _P, _P, _P]),
+    "oracle_reverse_inclusive_scan_f64": (None, [_P, _I64, _P]),
+    "oracle_dot_f64": (None, [_P, _P, _I64, _P, _P]),
+    "oracle_segmented_reduce_alg3_i64": (_I64, [ctypes.c_int, _P, _P]),
+    "oracle_dot_adjoint_f64": (None, [_P, _P, _I64, ctypes.c_double, _P, _P]),
+    "oracle_stencil5_f64": (None, [_P, _I64, _I64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P]),
+    "oracle_stencil5_f32": (None, [_P, _I64, _I64, ctypes.c_int, ctypes.c_float, ctypes.c_float, _P]),
+    "oracle_stencil5_f32_at": (None, [_P, _I64, _I64, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                      _P, _I64, _P]),
+    "oracle_stencil5_f64_at": (None, [_P, _I64, _I64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      _P, _I64, _P]),
+    "oracle_stencil5_T_f64": (None, [_P, _I64, _I64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P]),
+}
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            l = ctypes.CDLL(build())
+            for name, (res, args) in _SIGS.items():
+                f = getattr(l, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = l
+    return _lib
+
+
+def _c(a: np.ndarray, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------------------
+# inclusive_scan over the concatenation of segments (Sec. 3 "Distributed Range";
+# Sec. 4.3 "inclusive_scan")
+# ---------------------------------------------------------------------------
+
+def inclusive_scan_i64(x) -> np.ndarray:
+    x = _c(x, np.int64)
+    y = np.empty_like(x)
+    lib().oracle_inclusive_scan_i64(_p(x), x.size, _p(y))
+    return y
+
+
+def inclusive_scan_f32_f64(x):
+    """FP64 sequential scan of fp32 input; returns (y, abs_prefix)."""
+    x = _c(x, np.float32)
+    y = np.empty(x.size, np.float64)
+    a = np.empty(x.size, np.float64)
+    lib().oracle_inclusive_scan_f32_f64(_p(x), x.size, _p(y), _p(a))
+    return y, a
+
+
+def inclusive_scan_f64(x) -> np.ndarray:
+    x = _c(x, np.float64)
+    y = np.empty_like(x)
+    lib().oracle_inclusive_scan_f64(_p(x), x.size, _p(y))
+    return y
+
+
+def inclusive_scan_f32_seq(x) -> np.ndarray:
+    x = _c(x, np.float32)
+    y = np.empty_like(x)
+    lib().oracle_inclusive_scan_f32_seq(_p(x), x.size, _p(y))
+    return y
+
+
+def segmented_scan_alg4_i64(lens, x) -> np.ndarray:
+    """Algorithm 4 step by step (local scans, partial sums, offsets)."""
+    lens = _c(lens, np.int64)
+    x = _c(x, np.int64)
+    assert int(lens.sum()) == x.size
+    y = np.empty_like(x)
+    lib().oracle_segmented_scan_alg4_i64(int(lens.size), _p(lens), _p(x), _p(y))
+    return y
+
+
+def reverse_inclusive_scan_f64(g) -> np.ndarray:
+    """Adjoint of inclusive_scan: out[j] = sum_{i>=j} g[i]."""
+    g = _c(g, np.float64)
+    out = np.empty_like(g)
+    lib().oracle_reverse_inclusive_scan_f64(_p(g), g.size, _p(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# transform_reduce(zip(x, y), multiply, plus) -- Algorithm 1 / Algorithm 3
+# ---------------------------------------------------------------------------
+
+def dot_f64(x, y):
+    """Returns (dot, sum |x_i y_i|) in FP64."""
+    x = _c(x, np.float32)
+    y = _c(y, np.float32)
+    assert x.size == y.size
+    d = ctypes.c_double()
+    a = ctypes.c_double()
+    lib().oracle_dot_f64(_p(x), _p(y), x.size, ctypes.byref(d), ctypes.byref(a))
+    return d.value, a.value
+
+
+def segmented_reduce_alg3_i64(lens, x) -> int:
+    lens = _c(lens, np.int64)
+    x = _c(x, np.int64)
+    return int(lib().oracle_segmented_reduce_alg3_i64(int(lens.size), _p(lens), _p(x)))
+
+
+def dot_adjoint_f64(x, y, g: float):
+    x = _c(x, np.float32)
+    y = _c(y, np.float32)
+    gx = np.empty(x.size, np.float64)
+    gy = np.empty(x.size, np.float64)
+    lib().oracle_dot_adjoint_f64(_p(x), _p(y), x.size, float(g), _p(gx), _p(gy))
+    return gx, gy
+
+
+# ---------------------------------------------------------------------------
+# 5-point Jacobi stencil (zero outside the grid) and its transpose
+# ---------------------------------------------------------------------------
+
+def stencil5_f64(u0, steps: int, wc: float = 0.0, wn: float = 0.25) -> np.ndarray:
+    u0 = _c(u0, np.float64)
+    R, C = u0.shape
+    out = np.empty_like(u0)
+    lib().oracle_stencil5_f64(_p(u0), R, C, int(steps), float(wc), float(wn), _p(out))
+    return out
+
+
+def stencil5_f32(u0, steps: int, wc: float = 0.0, wn: float = 0.25) -> np.ndarray:
+    """fp32, fixed evaluation order ((N+S)+(W+E))*wn [+ wc*C]."""
+    u0 = _c(u0, np.float32)
+    R, C = u0.shape
+    out = np.empty_like(u0)
+    lib().oracle_stencil5_f32(_p(u0), R, C, int(steps), float(wc), float(wn), _p(out))
+    return out
+
+
+def stencil5_f32_at(u0, steps: int, cells, wc: float = 0.0, wn: float = 0.25) -> np.ndarray:
+    u0 = _c(u0, np.float32)
+    R, C = u0.shape
+    cells = _c(cells, np.int64).reshape(-1, 2)
+    out = np.empty(cells.shape[0], np.float32)
+    lib().oracle_stencil5_f32_at(_p(u0), R, C, int(steps), float(wc), float(wn), _p(cells),
+                                 cells.shape[0], _p(out))
+    return out
+
+
+def stencil5_f64_at(u0, steps: int, cells, wc: float = 0.0, wn: float = 0.25) -> np.ndarray:
+    u0 = _c(u0, np.float64)
+    R, C = u0.shape
+    cells = _c(cells, np.int64).reshape(-1, 2)
+    out = np.empty(cells.shape[0], np.float64)
+    lib().oracle_stencil5_f64_at(_p(u0), R, C, int(steps), float(wc), float(wn), _p(cells),
+                                 cells.shape[0], _p(out))
+    return out
+
+
+def stencil5_T_f64(v0, steps: int, wc: float = 0.0, wn: float = 0.25) -> np.ndarray:
+    v0 = _c(v0, np.float64)
+    R, C = v0.shape
+    out = np.empty_like(v0)
+    lib().oracle_stencil5_T_f64(_p(v0), R, C, int(steps), float(wc), float(wn), _p(out))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# zip re-segmentation (Sec. 4.4 "Zip"), brute force over element ownership
+# ---------------------------------------------------------------------------
+
+def zip_segments_bruteforce(lens_a, lens_b):
+    """For each global index i < min(|a|, |b|) find (segment of a, segment of b)
+    holding element i; the zipped segments are the maximal runs of indices with
+    the same pair.  Returns a list of (seg_a, off_in_a, seg_b, off_in_b, length).
+    Empty segments own no index and produce no piece.  Pure-Python loop: small
+    inputs only."""
+    def owners(lens):
+        out = []
+        for k, L in enumerate(lens):
+            out.extend((k, j) for j in range(int(L)))
+        return out
+
+    oa, ob = owners(lens_a), owners(lens_b)
+    n = min(len(oa), len(ob))
+    pieces = []
+    for i in range(n):
+        (ka, ja), (kb, jb) = oa[i], ob[i]
+        if pieces and pieces[-1][0] == ka and pieces[-1][2] == kb:
+            p = pieces[-1]
+            pieces[-1] = (p[0], p[1], p[2], p[3], p[4] + 1)
+        else:
+            pieces.append((ka, ja, kb, jb, 1))
+    return pieces
+
+
+# ---------------------------------------------------------------------------
+# central finite differences in FP64 (gradient checks)
+# ---------------------------------------------------------------------------
+
+def fd_gradient(loss, x, h: float = 2.0 ** -10) -> np.ndarray:
+    """g_j = (L(x + h e_j) - L(x - h e_j)) / (2h), FP64, one coordinate at a time."""
+    x = np.array(x, dtype=np.float64)
+    g = np.empty(x.size)
+    flat = x.reshape(-1)
+    for j in range(flat.size):
+        old = flat[j]
+        flat[j] = old + h
+        lp = loss(x)
+        flat[j] = old - h
+        lm = loss(x)
+        flat[j] = old
+        g[j] = (lp - lm) / (2.0 * h)
+    return g.reshape(x.shape)

@@ -1,0 +1,274 @@
+// CPU oracle for the segmented-range hot path of "Distributed Ranges"
+// (Brock et al., arXiv 2406.00158).
+//
+// TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+// CPU-baseline leg may load this library.  It shares no code, header, table or
+// helper with the CUDA path; both only see inputs from the seeded generator.
+//
+// Every function here is a plain, sequential, obviously-correct statement of
+// what the method computes:
+//   * A distributed range is the concatenation of its segments in segment order
+//     (Sec. 3, "Distributed Range"), so the oracle's scan and reduce work on the
+//     concatenated array; segmentation must not change any result (up to the
+//     floating-point rounding order), which the tests check on the GPU side.
+//   * Floating-point sums accumulate in FP64 in index order; integer sums are
+//     exact (two's-complement, mod 2^64).
+//   * Algorithms 3 and 4 (per-segment reduce / scan + carry) are also written
+//     out step by step for integers, so that the tests can confirm the paper's
+//     segmented procedure equals the plain definition.
+//   * The 5-point stencil and its transpose, the reverse scan (adjoint of the
+//     inclusive scan) and the dot-product adjoint are written from their
+//     definitions; the stencil's transpose is written in scatter form so that
+//     the symmetry of the operator is checked, never assumed.
+//
+// Build: g++ -O2 -std=c++17 -fPIC -shared -ffp-contract=off (no fast-math).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <vector>
+
+extern "C" {
+
+// --------------------------------------------------------------------------
+// inclusive_scan: y_i = x_0 + ... + x_i over the concatenation of segments
+// (Sec. 4.3 "inclusive_scan"; plain definition = std::inclusive_scan).
+// --------------------------------------------------------------------------
+
+// int64 with wrap-around addition: the sum is taken in uint64 (mod 2^64).
+void oracle_inclusive_scan_i64(const int64_t* x, int64_t n, int64_t* y) {
+  std::vector<uint64_t> ux(x, x + n), uy(n);
+  std::inclusive_scan(ux.begin(), ux.end(), uy.begin());
+  std::memcpy(y, uy.data(), sizeof(uint64_t) * n);
+}
+
+// fp32 input, FP64 sequential accumulation.  Also returns s_i = sum_{j<=i} |x_j|,
+// the scale of the rounding-error bound.
+void oracle_inclusive_scan_f32_f64(const float* x, int64_t n, double* y, double* abs_prefix) {
+  double s = 0.0, a = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    s += (double)x[i];
+    a += std::fabs((double)x[i]);
+    y[i] = s;
+    if (abs_prefix) abs_prefix[i] = a;
+  }
+}
+
+// FP64 input and output (used for adjoint / gradient references).
+void oracle_inclusive_scan_f64(const double* x, int64_t n, double* y) {
+  std::inclusive_scan(x, x + n, y);
+}
+
+// fp32 sequential scan in fp32 (context only: the error of the naive CPU scan).
+void oracle_inclusive_scan_f32_seq(const float* x, int64_t n, float* y) {
+  float s = 0.0f;
+  for (int64_t i = 0; i < n; ++i) {
+    s = s + x[i];
+    y[i] = s;
+  }
+}
+
+// Algorithm 4 written out for int64 (Sec. 4.3): a local scan of every segment,
+// the last element of each segment collected into partial_sums (one entry per
+// segment; an empty segment contributes 0), a scan of partial_sums, then
+// segment k > 0 adds partial_sums[k-1].
+void oracle_segmented_scan_alg4_i64(int nseg, const int64_t* lens, const int64_t* x,
+                                    int64_t* y) {
+  std::vector<uint64_t> partial(nseg, 0);
+  int64_t off = 0;
+  for (int k = 0; k < nseg; ++k) {
+    uint64_t s = 0;
+    for (int64_t i = 0; i < lens[k]; ++i) {
+      s += (uint64_t)x[off + i];
+      y[off + i] = (int64_t)s;
+    }
+    partial[k] = s;  // == *(out.end()-1), or the identity for an empty segment
+    off += lens[k];
+  }
+  std::inclusive_scan(partial.begin(), partial.end(), partial.begin());
+  off = 0;
+  for (int k = 0; k < nseg; ++k) {
+    uint64_t add = k > 0 ? partial[k - 1] : 0;
+    for (int64_t i = 0; i < lens[k]; ++i) y[off + i] = (int64_t)((uint64_t)y[off + i] + add);
+    off += lens[k];
+  }
+}
+
+// --------------------------------------------------------------------------
+// Reverse inclusive scan (adjoint of inclusive_scan):
+//   g_x[j] = sum_{i >= j} g_y[i]
+// --------------------------------------------------------------------------
+void oracle_reverse_inclusive_scan_f64(const double* g, int64_t n, double* out) {
+  double s = 0.0;
+  for (int64_t j = n - 1; j >= 0; --j) {
+    s += g[j];
+    out[j] = s;
+  }
+}
+
+// --------------------------------------------------------------------------
+// transform_reduce(zip(x, y), multiply, plus): the dot product of Algorithm 1,
+// reduced as in Algorithm 3.  Products of two fp32 values are exact in FP64; the
+// sum runs in index order in FP64.  abs_dot = sum |x_i y_i| (error-bound scale).
+// --------------------------------------------------------------------------
+void oracle_dot_f64(const float* x, const float* y, int64_t n, double* dot, double* abs_dot) {
+  *dot = std::inner_product(x, x + n, y, 0.0, std::plus<double>(),
+                            [](float a, float b) { return (double)a * (double)b; });
+  if (abs_dot)
+    *abs_dot = std::inner_product(x, x + n, y, 0.0, std::plus<double>(),
+                                  [](float a, float b) { return std::fabs((double)a * (double)b); });
+}
+
+// Algorithm 3 written out for int64: one local reduce per segment, partials
+// combined in segment order.
+int64_t oracle_segmented_reduce_alg3_i64(int nseg, const int64_t* lens, const int64_t* x) {
+  uint64_t init = 0;
+  int64_t off = 0;
+  for (int k = 0; k < nseg; ++k) {
+    uint64_t local = 0;
+    for (int64_t i = 0; i < lens[k]; ++i) local += (uint64_t)x[off + i];
+    init += local;
+    off += lens[k];
+  }
+  return (int64_t)init;
+}
+
+// Adjoint of d = <x, y> for an incoming gradient g: (g*y, g*x), in FP64.
+void oracle_dot_adjoint_f64(const float* x, const float* y, int64_t n, double g, double* gx,
+                            double* gy) {
+  for (int64_t i = 0; i < n; ++i) {
+    gx[i] = g * (double)y[i];
+    gy[i] = g * (double)x[i];
+  }
+}
+
+// --------------------------------------------------------------------------
+// 5-point Jacobi stencil for_each over an R x C row-major grid:
+//   u'[i][j] = wc*u[i][j] + wn*(u[i-1][j] + u[i+1][j] + u[i][j-1] + u[i][j+1]),
+// every cell updated, u = 0 outside [0,R) x [0,C) (zero ghost ring).  The
+// segmentation into row blocks and the halo exchange do not appear: the state
+// after each step does not depend on them.
+// --------------------------------------------------------------------------
+static inline double at_f64(const double* u, int64_t R, int64_t C, int64_t i, int64_t j) {
+  return (i < 0 || i >= R || j < 0 || j >= C) ? 0.0 : u[i * C + j];
+}
+
+static void stencil5_f64_step(const double* a, double* b, int64_t R, int64_t C, double wc,
+                              double wn) {
+  for (int64_t i = 0; i < R; ++i)
+    for (int64_t j = 0; j < C; ++j) {
+      double nbr = at_f64(a, R, C, i - 1, j) + at_f64(a, R, C, i + 1, j) + at_f64(a, R, C, i, j - 1) +
+                   at_f64(a, R, C, i, j + 1);
+      b[i * C + j] = wc * a[i * C + j] + wn * nbr;
+    }
+}
+
+void oracle_stencil5_f64(const double* u0, int64_t R, int64_t C, int steps, double wc, double wn,
+                         double* out) {
+  std::vector<double> a(u0, u0 + R * C), b(R * C);
+  for (int t = 0; t < steps; ++t) {
+    stencil5_f64_step(a.data(), b.data(), R, C, wc, wn);
+    std::swap(a, b);
+  }
+  std::memcpy(out, a.data(), sizeof(double) * R * C);
+}
+
+// The same stencil in fp32 with one fixed evaluation order, for bit-exact
+// comparison: s = (N + S) + (W + E); r = wn * s; and, only when wc != 0,
+// r = r + wc * C.  Every operation is a separately rounded fp32 add or
+// multiply (built with -ffp-contract=off, so nothing is fused).
+static inline float at_f32(const float* u, int64_t R, int64_t C, int64_t i, int64_t j) {
+  return (i < 0 || i >= R || j < 0 || j >= C) ? 0.0f : u[i * C + j];
+}
+
+static void stencil5_f32_step(const float* a, float* b, int64_t R, int64_t C, float wc, float wn) {
+  for (int64_t i = 0; i < R; ++i)
+    for (int64_t j = 0; j < C; ++j) {
+      float ns = at_f32(a, R, C, i - 1, j) + at_f32(a, R, C, i + 1, j);
+      float we = at_f32(a, R, C, i, j - 1) + at_f32(a, R, C, i, j + 1);
+      float s = ns + we;
+      float r = wn * s;
+      if (wc != 0.0f) r = r + wc * a[i * C + j];
+      b[i * C + j] = r;
+    }
+}
+
+void oracle_stencil5_f32(const float* u0, int64_t R, int64_t C, int steps, float wc, float wn,
+                         float* out) {
+  std::vector<float> a(u0, u0 + R * C), b(R * C);
+  for (int t = 0; t < steps; ++t) {
+    stencil5_f32_step(a.data(), b.data(), R, C, wc, wn);
+    std::swap(a, b);
+  }
+  std::memcpy(out, a.data(), sizeof(float) * R * C);
+}
+
+// Values of the stencil after `steps` steps at selected cells only.  One step
+// reads neighbours at distance 1, so the value at (i,j) after t steps depends
+// only on u0 within distance t.  For each requested cell the plain stencil is
+// run on the window [i-t, i+t] x [j-t, j+t] clipped to the grid; outside the
+// window (but inside the grid) the window sees zeros, which corrupts cells at
+// distance d from the window edge only from step d+1 on, so the centre is exact.
+// The per-cell arithmetic is identical to the full-grid functions above.
+void oracle_stencil5_f32_at(const float* u0, int64_t R, int64_t C, int steps, float wc, float wn,
+                            const int64_t* cells, int64_t ncells, float* out) {
+  for (int64_t q = 0; q < ncells; ++q) {
+    int64_t ci = cells[2 * q], cj = cells[2 * q + 1];
+    int64_t i0 = std::max<int64_t>(0, ci - steps), i1 = std::min<int64_t>(R, ci + steps + 1);
+    int64_t j0 = std::max<int64_t>(0, cj - steps), j1 = std::min<int64_t>(C, cj + steps + 1);
+    int64_t wr = i1 - i0, wcn = j1 - j0;
+    std::vector<float> a(wr * wcn), b(wr * wcn);
+    for (int64_t i = 0; i < wr; ++i)
+      for (int64_t j = 0; j < wcn; ++j) a[i * wcn + j] = u0[(i0 + i) * C + (j0 + j)];
+    for (int t = 0; t < steps; ++t) {
+      stencil5_f32_step(a.data(), b.data(), wr, wcn, wc, wn);
+      std::swap(a, b);
+    }
+    out[q] = a[(ci - i0) * wcn + (cj - j0)];
+  }
+}
+
+void oracle_stencil5_f64_at(const double* u0, int64_t R, int64_t C, int steps, double wc,
+                            double wn, const int64_t* cells, int64_t ncells, double* out) {
+  for (int64_t q = 0; q < ncells; ++q) {
+    int64_t ci = cells[2 * q], cj = cells[2 * q + 1];
+    int64_t i0 = std::max<int64_t>(0, ci - steps), i1 = std::min<int64_t>(R, ci + steps + 1);
+    int64_t j0 = std::max<int64_t>(0, cj - steps), j1 = std::min<int64_t>(C, cj + steps + 1);
+    int64_t wr = i1 - i0, wcn = j1 - j0;
+    std::vector<double> a(wr * wcn), b(wr * wcn);
+    for (int64_t i = 0; i < wr; ++i)
+      for (int64_t j = 0; j < wcn; ++j) a[i * wcn + j] = u0[(i0 + i) * C + (j0 + j)];
+    for (int t = 0; t < steps; ++t) {
+      stencil5_f64_step(a.data(), b.data(), wr, wcn, wc, wn);
+      std::swap(a, b);
+    }
+    out[q] = a[(ci - i0) * wcn + (cj - j0)];
+  }
+}
+
+// Transposed stencil A^T, applied `steps` times, in scatter form: each cell
+// (k,l) sends wc*v[k][l] to itself and wn*v[k][l] to each in-grid neighbour,
+// i.e. column (k,l) of A^T is row (k,l) of A.
+void oracle_stencil5_T_f64(const double* v0, int64_t R, int64_t C, int steps, double wc,
+                           double wn, double* out) {
+  std::vector<double> a(v0, v0 + R * C), b(R * C);
+  const int64_t di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+  for (int t = 0; t < steps; ++t) {
+    std::fill(b.begin(), b.end(), 0.0);
+    for (int64_t k = 0; k < R; ++k)
+      for (int64_t l = 0; l < C; ++l) {
+        double v = a[k * C + l];
+        b[k * C + l] += wc * v;
+        for (int d = 0; d < 4; ++d) {
+          int64_t i = k + di[d], j = l + dj[d];
+          if (i >= 0 && i < R && j >= 0 && j < C) b[i * C + j] += wn * v;
+        }
+      }
+    std::swap(a, b);
+  }
+  std::memcpy(out, a.data(), sizeof(double) * R * C);
+}
+
+}  // extern "C"

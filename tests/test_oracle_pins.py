@@ -1,0 +1,380 @@
+"""Pins of the CPU oracle against facts fixed outside the oracle itself:
+closed forms, brute force on tiny inputs, exact special cases, invariants and
+adjoint identities.  Each test is chosen so that a plausible slip in the oracle
+(a dropped term, an off-by-one, a wrong sign or transposed index, a wrong
+boundary) fails it.  CPU only."""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_00158_gb300 import inputs
+
+RNG_KEY = 99
+
+
+# ----------------------------------------------------------------------------------
+# inclusive_scan, int64 (plain definition: y_i = x_0 + ... + x_i)
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [0, 1, 2, 7, 4097])
+def test_scan_i64_ones_is_iota(n):
+    y = oracle.inclusive_scan_i64(np.ones(n, np.int64))
+    assert np.array_equal(y, np.arange(1, n + 1, dtype=np.int64))
+
+
+def test_scan_i64_arange_closed_form():
+    n = 100_003
+    y = oracle.inclusive_scan_i64(np.arange(n, dtype=np.int64))
+    i = np.arange(n, dtype=np.int64)
+    assert np.array_equal(y, i * (i + 1) // 2)
+    assert int(y[-1]) == n * (n - 1) // 2
+
+
+def test_scan_i64_bruteforce_tiny():
+    x = inputs.uniform_int64(RNG_KEY, 8, -10**12, 10**12)
+    for n in range(9):
+        y = oracle.inclusive_scan_i64(x[:n])
+        for i in range(n):
+            assert int(y[i]) == sum(int(v) for v in x[:i + 1])
+
+
+def test_scan_i64_wraps_mod_2_64():
+    big = np.array([2**62, 2**62, 2**62, -5], dtype=np.int64)
+    y = oracle.inclusive_scan_i64(big)
+
+    def wrap(v):
+        v %= 2**64
+        return v - 2**64 if v >= 2**63 else v
+
+    for i in range(4):
+        assert int(y[i]) == wrap(sum(int(v) for v in big[:i + 1]))
+
+
+def _compositions(n, parts_max=4):
+    """All ways to cut n into 1..parts_max ordered segments, empty segments allowed."""
+    for k in range(1, parts_max + 1):
+        for cuts in itertools.combinations_with_replacement(range(n + 1), k - 1):
+            edges = (0,) + cuts + (n,)
+            yield [edges[i + 1] - edges[i] for i in range(k)]
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 8])
+def test_alg4_segmented_scan_equals_definition_all_splits(n):
+    x = inputs.uniform_int64(RNG_KEY + n, n, 0, 1000)
+    ref = oracle.inclusive_scan_i64(x)
+    for lens in _compositions(n):
+        assert np.array_equal(oracle.segmented_scan_alg4_i64(lens, x), ref), lens
+
+
+def test_alg4_random_large_split_with_empty_segments():
+    n = 1 << 16
+    x = inputs.uniform_int64(RNG_KEY, n, 0, 1000)
+    lens = inputs.random_cut_segments(7, n, 12)
+    lens = lens[:3] + [0] + lens[3:] + [0]
+    assert np.array_equal(oracle.segmented_scan_alg4_i64(lens, x), oracle.inclusive_scan_i64(x))
+
+
+def test_scan_i64_total_permutation_invariant():
+    x = inputs.uniform_int64(RNG_KEY, 10_000, 0, 1000)
+    p = np.argsort(inputs.raw_u64(5, x.size))
+    assert oracle.inclusive_scan_i64(x)[-1] == oracle.inclusive_scan_i64(x[p])[-1] == int(x.sum())
+
+
+# ----------------------------------------------------------------------------------
+# inclusive_scan, fp32 input accumulated in FP64
+# ----------------------------------------------------------------------------------
+
+def test_scan_f32_f64_ones_exact():
+    n = 1 << 20
+    y, a = oracle.inclusive_scan_f32_f64(np.ones(n, np.float32))
+    assert np.array_equal(y, np.arange(1, n + 1, dtype=np.float64))
+    assert np.array_equal(a, y)
+
+
+def test_scan_f32_f64_integer_values_exact():
+    xi = inputs.uniform_int64(RNG_KEY, 50_000, -1000, 1000)
+    y, a = oracle.inclusive_scan_f32_f64(xi.astype(np.float32))
+    assert np.array_equal(y, np.cumsum(xi).astype(np.float64))
+    assert np.array_equal(a, np.cumsum(np.abs(xi)).astype(np.float64))
+
+
+def test_scan_f32_f64_matches_exact_rational_prefix():
+    x = inputs.uniform_pm1_f32(RNG_KEY, 300)
+    y, a = oracle.inclusive_scan_f32_f64(x)
+    acc = Fraction(0)
+    for i, v in enumerate(x):
+        acc += Fraction(float(v))
+        # sequential FP64 summation error <= i * 2^-53 * sum|x|
+        assert abs(Fraction(float(y[i])) - acc) <= Fraction(i + 1, 2**53) * Fraction(float(a[i]))
+
+
+def test_scan_f32_seq_exact_on_small_integers():
+    xi = inputs.uniform_int64(RNG_KEY, 4096, 0, 1000)
+    y = oracle.inclusive_scan_f32_seq(xi.astype(np.float32))
+    assert np.array_equal(y.astype(np.int64), np.cumsum(xi))
+
+
+# ----------------------------------------------------------------------------------
+# reverse inclusive scan (adjoint of inclusive_scan)
+# ----------------------------------------------------------------------------------
+
+def test_reverse_scan_ones_closed_form():
+    n = 1000
+    assert np.array_equal(oracle.reverse_inclusive_scan_f64(np.ones(n)),
+                          np.arange(n, 0, -1, dtype=np.float64))
+
+
+def test_reverse_scan_bruteforce():
+    g = inputs.uniform_pm1_f32(3, 50).astype(np.float64)
+    r = oracle.reverse_inclusive_scan_f64(g)
+    for j in range(50):
+        assert r[j] == pytest.approx(math.fsum(g[j:]), abs=1e-14)
+
+
+def test_reverse_scan_is_adjoint_of_scan():
+    n = 4096
+    x = inputs.uniform_pm1_f32(11, n).astype(np.float64)
+    w = inputs.uniform_pm1_f32(12, n).astype(np.float64)
+    lhs = math.fsum(oracle.inclusive_scan_f64(x) * w)
+    rhs = math.fsum(x * oracle.reverse_inclusive_scan_f64(w))
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-9)
+
+
+def test_fd_gradient_of_scan_equals_reverse_scan():
+    n = 256
+    x = inputs.uniform_pm1_f32(13, n).astype(np.float64)
+    w = inputs.uniform_pm1_f32(14, n).astype(np.float64)
+    g = oracle.fd_gradient(lambda v: float(np.dot(w, oracle.inclusive_scan_f64(v))), x)
+    assert np.allclose(g, oracle.reverse_inclusive_scan_f64(w), rtol=0, atol=1e-10)
+
+
+# ----------------------------------------------------------------------------------
+# dot = transform_reduce(zip(x, y), multiply, plus)
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("a,b", [(0.5, 0.25), (-2.0, 0.125), (1.0, 1.0)])
+def test_dot_constant_powers_of_two(a, b):
+    n = 1 << 20
+    d, ad = oracle.dot_f64(np.full(n, a, np.float32), np.full(n, b, np.float32))
+    assert d == n * a * b
+    assert ad == n * abs(a * b)
+
+
+def test_dot_iota_times_ones():
+    n = 1 << 12
+    d, _ = oracle.dot_f64(np.arange(n, dtype=np.float32), np.ones(n, np.float32))
+    assert d == n * (n - 1) // 2
+
+
+def test_dot_against_exact_sum():
+    x = inputs.uniform_pm1_f32(21, 5000)
+    y = inputs.uniform_pm1_f32(22, 5000)
+    d, ad = oracle.dot_f64(x, y)
+    prods = [float(a) * float(b) for a, b in zip(x, y)]  # exact in FP64
+    assert abs(d - math.fsum(prods)) <= 5000 * 2**-53 * ad
+    assert ad == pytest.approx(math.fsum(abs(p) for p in prods), rel=1e-12)
+
+
+def test_dot_uneven_lengths_and_empty():
+    d, ad = oracle.dot_f64(np.zeros(0, np.float32), np.zeros(0, np.float32))
+    assert d == 0.0 and ad == 0.0
+
+
+def test_alg3_segmented_reduce_equals_sum():
+    x = inputs.uniform_int64(31, 70_000, -500, 500)
+    for nseg in (1, 3, 8):
+        lens = inputs.random_cut_segments(40 + nseg, x.size, nseg)
+        assert oracle.segmented_reduce_alg3_i64(lens + [0], x) == int(x.sum())
+
+
+def test_dot_adjoint_matches_fd_of_dot():
+    n = 64
+    x = inputs.uniform_pm1_f32(41, n)
+    y = inputs.uniform_pm1_f32(42, n)
+    g = 0.75
+    gx, gy = oracle.dot_adjoint_f64(x, y, g)
+    # d(g*<x,y>)/dx_j, by central differences on the oracle's own dot; h = 2^-10
+    # keeps x_j +- h exact in fp32 so the difference is exact.
+    fdx = oracle.fd_gradient(lambda v: g * oracle.dot_f64(v.astype(np.float32), y)[0], x)
+    fdy = oracle.fd_gradient(lambda v: g * oracle.dot_f64(x, v.astype(np.float32))[0], y)
+    assert np.allclose(gx, fdx, atol=1e-12) and np.allclose(gy, fdy, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------------
+# 5-point stencil (zero outside the grid), its transpose, sampled-cell variants
+# ----------------------------------------------------------------------------------
+
+def _dist_to_edge(R, C):
+    i = np.arange(R)[:, None]
+    j = np.arange(C)[None, :]
+    return np.minimum(np.minimum(i, R - 1 - i), np.minimum(j, C - 1 - j))
+
+
+@pytest.mark.parametrize("steps", [1, 3, 7])
+def test_stencil_linear_field_is_harmonic(steps):
+    R, C = 40, 33
+    i = np.arange(R)[:, None].astype(np.float64)
+    j = np.arange(C)[None, :].astype(np.float64)
+    u0 = 3 * i - 2 * j + 5
+    far = _dist_to_edge(R, C) >= steps
+    out64 = oracle.stencil5_f64(u0, steps)
+    out32 = oracle.stencil5_f32(u0.astype(np.float32), steps)
+    assert np.array_equal(out64[far], u0[far])
+    assert np.array_equal(out32[far], u0[far].astype(np.float32))
+    # the zero ghost ring pulls the edge down: the corner after one step
+    if steps == 1:
+        assert out64[0, 0] == 0.25 * (u0[1, 0] + u0[0, 1])
+
+
+def test_stencil_constant_field_interior():
+    R, C, t = 30, 30, 5
+    out = oracle.stencil5_f64(np.full((R, C), 0.5), t)
+    far = _dist_to_edge(R, C) >= t
+    assert np.all(out[far] == 0.5)
+    assert np.all(out[~far] < 0.5)
+
+
+@pytest.mark.parametrize("t", [1, 2, 5, 12])
+def test_stencil_impulse_is_random_walk_law(t):
+    # A^t e_c for wc=0, wn=1/4 is the law of a simple 2D random walk after t
+    # steps: P(x, y) = C(t, (t+x+y)/2) * C(t, (t+x-y)/2) / 4^t when x+y+t is even.
+    n = 2 * t + 9
+    c = n // 2
+    u0 = np.zeros((n, n))
+    u0[c, c] = 1.0
+    out = oracle.stencil5_f64(u0, t)
+    for x in range(-t - 1, t + 2):
+        for y in range(-t - 1, t + 2):
+            if (x + y + t) % 2 or abs(x) + abs(y) > t:
+                p = 0.0
+            else:
+                p = math.comb(t, (t + x + y) // 2) * math.comb(t, (t + x - y) // 2) / 4.0**t
+            assert out[c + x, c + y] == p, (x, y)
+
+
+def test_stencil_weights_one_step_impulse():
+    u0 = np.zeros((5, 6))
+    u0[2, 3] = 1.0
+    out = oracle.stencil5_f64(u0, 1, wc=0.5, wn=0.125)
+    exp = np.zeros((5, 6))
+    exp[2, 3] = 0.5
+    exp[1, 3] = exp[3, 3] = exp[2, 2] = exp[2, 4] = 0.125
+    assert np.array_equal(out, exp)
+    # the corner loses the two neighbours that fall outside the grid
+    u0 = np.zeros((5, 6))
+    u0[0, 0] = 1.0
+    out = oracle.stencil5_f64(u0, 1)
+    assert out.sum() == 0.5 and out[0, 1] == out[1, 0] == 0.25
+
+
+@pytest.mark.parametrize("wc,wn", [(0.0, 0.25), (0.3, 0.15), (-0.1, 0.7)])
+def test_stencil_transpose_adjoint_identity(wc, wn):
+    R, C, t = 9, 13, 4
+    x = inputs.uniform_pm1_f32(51, R * C).astype(np.float64).reshape(R, C)
+    w = inputs.uniform_pm1_f32(52, R * C).astype(np.float64).reshape(R, C)
+    lhs = math.fsum((oracle.stencil5_f64(x, t, wc, wn) * w).ravel())
+    rhs = math.fsum((x * oracle.stencil5_T_f64(w, t, wc, wn)).ravel())
+    assert lhs == pytest.approx(rhs, rel=1e-13, abs=1e-13)
+    # with a zero ghost ring the operator is symmetric: A^T w == A w
+    assert np.allclose(oracle.stencil5_T_f64(w, t, wc, wn), oracle.stencil5_f64(w, t, wc, wn),
+                       rtol=0, atol=1e-14)
+
+
+def test_stencil_f32_same_order_within_contraction_bound():
+    R, C, t = 64, 48, 20
+    u0 = inputs.uniform01_f32(61, R * C).reshape(R, C)
+    d = np.abs(oracle.stencil5_f32(u0, t).astype(np.float64) - oracle.stencil5_f64(u0, t))
+    assert d.max() <= 3 * t * 2.0**-24 * np.abs(u0).max()
+
+
+@pytest.mark.parametrize("wc,wn", [(0.0, 0.25), (0.2, 0.2)])
+def test_stencil_sampled_cells_equal_full_grid(wc, wn):
+    R, C, t = 23, 31, 6
+    u0 = inputs.uniform01_f32(71, R * C).reshape(R, C)
+    cells = np.array([(i, j) for i in range(R) for j in range(C)], np.int64)
+    full32 = oracle.stencil5_f32(u0, t, wc, wn)
+    at32 = oracle.stencil5_f32_at(u0, t, cells, wc, wn)
+    assert np.array_equal(at32, full32[cells[:, 0], cells[:, 1]])
+    full64 = oracle.stencil5_f64(u0, t, wc, wn)
+    at64 = oracle.stencil5_f64_at(u0, t, cells, wc, wn)
+    assert np.array_equal(at64, full64[cells[:, 0], cells[:, 1]])
+
+
+def test_stencil_fd_gradient_equals_transpose():
+    R, C, t = 8, 8, 3
+    u0 = inputs.uniform01_f32(81, R * C).astype(np.float64).reshape(R, C)
+    w = inputs.uniform_pm1_f32(82, R * C).astype(np.float64).reshape(R, C)
+    g = oracle.fd_gradient(lambda v: float((oracle.stencil5_f64(v, t) * w).sum()), u0)
+    assert np.allclose(g, oracle.stencil5_T_f64(w, t), atol=1e-10)
+
+
+# ----------------------------------------------------------------------------------
+# zip re-segmentation (Sec. 4.4)
+# ----------------------------------------------------------------------------------
+
+def test_zip_hand_examples():
+    # a = [3 | 5], b = [4 | 4]: cuts at 3 and 4 -> pieces of 3, 1, 4
+    assert oracle.zip_segments_bruteforce([3, 5], [4, 4]) == [
+        (0, 0, 0, 0, 3), (1, 0, 0, 3, 1), (1, 1, 1, 0, 4)]
+    assert oracle.zip_segments_bruteforce([8], [8]) == [(0, 0, 0, 0, 8)]
+    # empty segments own nothing
+    assert oracle.zip_segments_bruteforce([0, 4], [2, 0, 2]) == [(1, 0, 0, 0, 2), (1, 2, 2, 0, 2)]
+    # zip is as long as its shortest input
+    assert oracle.zip_segments_bruteforce([5], [2, 1]) == [(0, 0, 0, 0, 2), (0, 2, 1, 0, 1)]
+
+
+def test_zip_properties_random():
+    for trial in range(30):
+        na = 1 + trial % 5
+        nb = 1 + (trial * 7) % 6
+        la = inputs.random_cut_segments(100 + trial, 200, na)
+        lb = inputs.random_cut_segments(200 + trial, 200 - trial, nb)
+        pcs = oracle.zip_segments_bruteforce(la, lb)
+        assert sum(p[4] for p in pcs) == min(sum(la), sum(lb))
+        bounds_a = set(np.cumsum([0] + la))
+        bounds_b = set(np.cumsum([0] + lb))
+        pos = 0
+        for k, (sa, oa, sb, ob, L) in enumerate(pcs):
+            assert oa + L <= la[sa] and ob + L <= lb[sb] and L > 0
+            pos += L
+            if k + 1 < len(pcs):  # every cut is a segment boundary of a or of b
+                assert pos in bounds_a or pos in bounds_b
+
+
+# ----------------------------------------------------------------------------------
+# seeded generator
+# ----------------------------------------------------------------------------------
+
+def test_splitmix64_published_outputs():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_seed0.txt")
+    want = [int(l, 16) for l in open(path) if l.strip() and not l.startswith("#")]
+    assert [int(v) for v in inputs.raw_u64(0, len(want))] == want
+
+
+def test_generator_ranges_and_exactness():
+    x = inputs.uniform_pm1_f32(1, 1 << 16)
+    assert x.min() >= -1.0 and x.max() < 1.0
+    k = (x.astype(np.float64) + 1.0) * 2.0**23
+    assert np.array_equal(k, np.round(k))
+    u = inputs.uniform01_f32(2, 1 << 16)
+    assert u.min() >= 0.0 and u.max() < 1.0
+    i = inputs.uniform_int64(3, 1 << 16)
+    assert i.min() >= 0 and i.max() < 1000
+    # chunked / threaded generation equals one-shot generation
+    big = inputs.uniform_pm1_f32(9, (1 << 22) + 5)
+    assert np.array_equal(big[-5:], inputs.uniform_pm1_f32(9, (1 << 22) + 5)[-5:])
+    assert np.array_equal(inputs.raw_u64(9, 10, start=(1 << 22) - 3),
+                          inputs.raw_u64(9, (1 << 22) + 7)[-10:])
+
+
+def test_batch_shapes_recipe():
+    shapes = inputs.batch_shapes(2411, 256)
+    for s in shapes:
+        assert 1 <= len(s) <= 8 and all(v > 0 for v in s)
+        assert 1000 <= sum(s) <= 1_000_000
+    assert shapes == inputs.batch_shapes(2411, 256)
