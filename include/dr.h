@@ -1,0 +1,304 @@
+/*
+ * dr.h -- C ABI of a GB300-native (sm_103a) implementation of the data-parallel
+ * hot path of the Distributed Ranges model (Brock, Cohn, et al., arXiv 2406.00158).
+ *
+ * Model (Sec. 3): a *distributed range* is a range split into *segments*; each
+ * segment is a *remote range* living in one memory locale, and the segments
+ * concatenated in order form the whole range.  Here every memory locale is a
+ * separate allocation in one GPU's HBM, so a segment is just (device pointer,
+ * length).  Containers are built over caller-given segments, *views* are
+ * composed lazily (Sec. 4.4: transform, zip) and algorithms (Sec. 4.3:
+ * inclusive_scan, reduce / transform_reduce, for_each) run over a composition
+ * with the view fused into the kernel's loads and stores.
+ *
+ * Conventions for every entry point:
+ *   - Returns an int status (enum dr_status); never throws or aborts across
+ *     the ABI.  On failure, dr_last_error() gives a message for this thread.
+ *   - Device memory is OWNED BY THE CALLER and never freed by the library.
+ *     Handles (dr_vec, dr_md2, dr_view, dr_batch) are owned by the library from
+ *     *_create / *_plan until the matching *_destroy.
+ *   - Views are non-owning (Sec. 4.4): a view must not outlive the containers
+ *     (or views) it was built from.
+ *   - Every GPU call is asynchronous on the stream it is given (NULL = the
+ *     legacy default stream) and uses the calling thread's current CUDA device.
+ *     Device-side failures (a bounded wait that expired) are recorded in a
+ *     per-device status word that dr_sync_status() reads and clears.
+ *   - A handle that carries device workspace (views passed to algorithms,
+ *     batch plans) must not be used by two calls that can overlap on the GPU.
+ *   - Element types: fp32, fp64, int64, int32.  Integer arithmetic wraps mod
+ *     2^bits; floating-point arithmetic is IEEE round-to-nearest, no fast-math.
+ */
+#ifndef DR_GB300_H
+#define DR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* dr_stream_t;
+
+enum dr_status {
+  DR_OK = 0,
+  DR_E_INVAL = 1,       /* bad argument: null pointer, negative size, size mismatch */
+  DR_E_DTYPE = 2,       /* unsupported or mismatched element type / operation */
+  DR_E_ALIGN = 3,       /* pointer not aligned to its element size, or a non-aligned
+                           zip where strict alignment was requested (Sec. 4.3) */
+  DR_E_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error) */
+  DR_E_TIMEOUT = 5,     /* a bounded device-side wait expired (see dr_set_spin_limit) */
+  DR_E_BOUNDS = 6,      /* index out of range */
+  DR_E_NOMEM = 7,       /* workspace allocation failed */
+  DR_E_UNSUPPORTED = 8  /* composition or size outside what this build supports */
+};
+
+enum dr_dtype { DR_F32 = 0, DR_F64 = 1, DR_I64 = 2, DR_I32 = 3 };
+
+/* Associative binary operations (scan / reduce operators, zip combiners).
+ * Sec. 4.3 (footnote to "reduce") allows any such operator; PLUS is the one
+ * of Algorithms 1, 3 and 4. */
+enum dr_binop { DR_PLUS = 0, DR_MUL = 1, DR_MIN = 2, DR_MAX = 3 };
+
+/* Elementwise functions of a transform view (Sec. 4.4 "Transform");
+ * `arg` is the scalar a. */
+enum dr_unop {
+  DR_U_SCALE = 0,  /* a * x */
+  DR_U_ADD = 1,    /* x + a */
+  DR_U_NEG = 2,    /* -x */
+  DR_U_ABS = 3,    /* |x| */
+  DR_U_SQUARE = 4  /* x * x */
+};
+
+typedef struct dr_vec dr_vec;
+typedef struct dr_md2 dr_md2;
+typedef struct dr_view dr_view;
+typedef struct dr_batch dr_batch;
+
+/* One piece of a view's segmentation, as reported by dr_view_segments: the
+ * piece covers `len` consecutive elements of the view starting at global index
+ * `start`; for each operand k (k < arity) it lies in segment seg[k] of that
+ * operand's container, starting at element off[k] of that segment. */
+typedef struct dr_piece {
+  int64_t start;
+  int64_t len;
+  int32_t seg[2];
+  int64_t off[2];
+} dr_piece;
+
+/* Launch shape of the batched kernel (chosen by the autotuner or the caller). */
+typedef struct dr_tune {
+  int32_t threads;      /* threads per CTA: 128, 256 or 512 */
+  int32_t items;        /* elements per thread per tile: 8 or 16 (fp32) */
+  int32_t ctas_per_sm;  /* persistent CTAs per SM: 1..8 */
+} dr_tune;
+
+/* ------------------------------------------------------------------------ */
+/* Library status                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Message of the last failed call on this thread (never NULL; "" if none). */
+const char* dr_last_error(void);
+
+/* ABI version, currently 1. */
+int dr_version(void);
+
+/* Synchronizes `stream`, then reads and clears the current device's status
+ * word.  Returns DR_OK, DR_E_TIMEOUT (a bounded wait expired in a kernel
+ * launched earlier on this device; its results are invalid) or DR_E_CUDA. */
+int dr_sync_status(dr_stream_t stream);
+
+/* Upper bound on the polls of every device-side wait (scan lookback, batched
+ * carry); each poll sleeps at most ~1 us.  Default 1<<21 (~1-2 s).  polls>=1. */
+int dr_set_spin_limit(int64_t polls);
+
+/* Test hook for the bounded-wait path: the next scan launch skips publishing
+ * the status of tile `tile` (so its successors' waits expire and report
+ * DR_E_TIMEOUT instead of hanging).  tile < 0 disarms.  Not for production. */
+int dr_debug_skip_publish(int64_t tile);
+
+/* ------------------------------------------------------------------------ */
+/* Segmented vector (Sec. 4.2.1 "Distributed Vector")                        */
+/* ------------------------------------------------------------------------ */
+
+/* Block partition of Sec. 4.2.1: p segments of ceil(n/p) elements, the last
+ * ones shorter or empty.  Writes p lengths to lens_out.  Host only. */
+int dr_block_lengths(int64_t n, int p, int64_t* lens_out);
+
+/* Builds a segmented vector over nseg caller-owned device segments:
+ * segment k holds lens[k] >= 0 elements of `dtype` at seg_ptrs[k] (which may
+ * be NULL only if lens[k] == 0 and must be aligned to the element size;
+ * 16-byte alignment enables 128-bit access).  The global order is segment 0,
+ * then 1, ... (the concatenation of Sec. 3).  nseg >= 1.  Host only: the
+ * pointers are recorded, not dereferenced. */
+int dr_vec_create(int dtype, int nseg, const int64_t* lens, void* const* seg_ptrs, dr_vec** out);
+int dr_vec_destroy(dr_vec* v);
+
+/* Shape queries (host only). */
+int dr_vec_info(const dr_vec* v, int* dtype, int* nseg, int64_t* n);
+int dr_vec_segment(const dr_vec* v, int k, void** ptr, int64_t* len, int64_t* start);
+
+/* Global index arithmetic of operator[] (Sec. 4.2): element i of the vector is
+ * element *off of segment *seg.  DR_E_BOUNDS unless 0 <= i < n.  Host only. */
+int dr_vec_locate(const dr_vec* v, int64_t i, int* seg, int64_t* off);
+
+/* Copies the whole vector from / to a contiguous host buffer of n elements
+ * (pinned memory makes the copies asynchronous), one cudaMemcpyAsync per
+ * segment, on `stream` (Sec. 4.1: copy into and out of remote memory). */
+int dr_vec_copy_from_host(dr_vec* v, const void* host, dr_stream_t stream);
+int dr_vec_copy_to_host(const dr_vec* v, void* host, dr_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Row-block segmented 2-D array (Sec. 4.2.2 "Distributed Matrix", block_row  */
+/* partition) with one ghost (halo) row above and below every segment.        */
+/* ------------------------------------------------------------------------ */
+
+/* rows x cols array in nseg row blocks; block k has seg_rows[k] >= 1 rows and
+ * seg_ptrs[k] points to (seg_rows[k] + 2) * cols contiguous elements: row 0 is
+ * the top ghost row, rows 1..seg_rows[k] the block's own rows, row
+ * seg_rows[k]+1 the bottom ghost row.  sum(seg_rows) == rows.  Only DR_F32.
+ * Ghost rows hold copies of the neighbouring blocks' boundary rows; the
+ * ghosts at the two outer edges of the grid are never read (the grid is zero
+ * outside).  The library rewrites ghost rows of any array it operates on. */
+int dr_md2_create(int dtype, int64_t rows, int64_t cols, int nseg, const int64_t* seg_rows,
+                  void* const* seg_ptrs, dr_md2** out);
+int dr_md2_destroy(dr_md2* m);
+
+/* Halo exchange: copies each block's first / last own row into the ghost row
+ * of the neighbouring block, on `stream`. */
+int dr_md2_exchange_halos(dr_md2* m, dr_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Views (Sec. 4.4).  Lazy, non-owning, composable.                          */
+/* ------------------------------------------------------------------------ */
+
+/* The view of a whole vector. */
+int dr_view_of(const dr_vec* v, dr_view** out);
+
+/* transform: applies `op` (enum dr_unop, scalar `arg`) to every element of a
+ * single-valued view.  Its segments are the base's segments, transformed. */
+int dr_view_transform(const dr_view* base, int op, double arg, dr_view** out);
+
+/* zip of two single-valued views of the same dtype: element i is the pair
+ * (a_i, b_i), length min(|a|, |b|).  If the operands are not aligned (same
+ * segment count and sizes) the segments are re-cut at the union of both
+ * operands' boundaries (Sec. 4.4 "Zip").  A zip is not single-valued until a
+ * binary function is applied with dr_view_zip_transform. */
+int dr_view_zip(const dr_view* a, const dr_view* b, dr_view** out);
+
+/* transform of a zip with a binary function: element i = op(a_i, b_i), e.g.
+ * DR_MUL for the dot product of Algorithm 1. */
+int dr_view_zip_transform(const dr_view* zip, int op, dr_view** out);
+
+/* take / drop (Sec. 4.4 "Take and Drop"): the first l elements, or all but the
+ * first f, via trimmed segments.  l and f are clamped to [0, size]. */
+int dr_view_take(const dr_view* base, int64_t l, dr_view** out);
+int dr_view_drop(const dr_view* base, int64_t f, dr_view** out);
+
+int dr_view_destroy(dr_view* v);
+
+/* Queries (host only): size, arity (1 for single-valued, 2 for a raw zip),
+ * element type, number of pieces of the (re-)segmentation, and the pieces. */
+int dr_view_info(const dr_view* v, int64_t* size, int* arity, int* dtype, int* npieces);
+int dr_view_segments(const dr_view* v, int max_pieces, dr_piece* out);
+
+/* ------------------------------------------------------------------------ */
+/* Algorithms (Sec. 4.3)                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* inclusive_scan (Sec. 4.3, Algorithm 4): out_i = in_0 op in_1 op ... op in_i
+ * over the whole range, across segment boundaries, op in {PLUS, MIN, MAX}.
+ * `in` is single-valued; `out` has in's dtype and at least |in| elements; out
+ * may be the same storage as in's base vector (in place).  Single pass: each
+ * tile's carry comes from its predecessors' published aggregates (decoupled
+ * lookback) instead of Algorithm 4's second pass over the data.  The first
+ * call on a view allocates its workspace (do it outside stream capture). */
+int dr_inclusive_scan(const dr_view* in, dr_vec* out, int op, dr_stream_t stream);
+
+/* exclusive_scan (Sec. 4.3, last paragraph of "inclusive_scan"): out_0 = init,
+ * out_i = init op in_0 op ... op in_{i-1}.  `init` points to one host value of
+ * the view's dtype. */
+int dr_exclusive_scan(const dr_view* in, dr_vec* out, int op, const void* init,
+                      dr_stream_t stream);
+
+/* Reverse inclusive scan: out_j = in_j + in_{j+1} + ... + in_{n-1}.  This is
+ * the adjoint of the PLUS inclusive scan (gradient of y = scan(x) is
+ * x_bar = reverse_scan(y_bar)). */
+int dr_reverse_inclusive_scan(const dr_view* in, dr_vec* out, dr_stream_t stream);
+
+/* reduce / transform_reduce (Sec. 4.3, Algorithm 3; Algorithm 1's dot product
+ * is transform_reduce over zip_transform(zip(x, y), MUL) with PLUS):
+ * *dev_result = init op in_0 op ... op in_{n-1}.  `init` points to one host
+ * value of the view's dtype; dev_result to one device element.  One kernel:
+ * per-CTA partials combined by the last CTA in a fixed order (deterministic
+ * for a given device).  Workspace as for dr_inclusive_scan. */
+int dr_transform_reduce(const dr_view* in, int op, const void* init, void* dev_result,
+                        dr_stream_t stream);
+
+/* Adjoint of d = <x, y> (dot product): gx = g * y and gy = g * x elementwise,
+ * with g read from device memory (dev_g, one fp32).  Either output may be
+ * NULL.  fp32 vectors of equal length; segmentations may differ. */
+int dr_scale_by_partner(const dr_vec* x, const dr_vec* y, const float* dev_g, dr_vec* gx,
+                        dr_vec* gy, dr_stream_t stream);
+
+/* for_each with a 5-point Jacobi update (a halo-exchanging stencil over the
+ * row-block array; Sec. 4.3 "for_each" over Sec. 4.2.2's block-row matrix):
+ *   u'[i][j] = wc*u[i][j] + wn*(u[i-1][j] + u[i+1][j] + u[i][j-1] + u[i][j+1])
+ * on every cell, with u = 0 outside the grid, evaluated in fp32 as
+ * s = (N + S) + (W + E); r = wn*s; if wc != 0: r = r + wc*C (no fusion).
+ * Runs `steps` >= 1 steps from `in`; the result lands in `out`; `tmp` (same
+ * shape; may be NULL when steps == 1) holds intermediate states.  The first
+ * step re-exchanges in's halos; every step writes its blocks' boundary rows
+ * into the neighbours' ghost rows of its output.  in, out, tmp distinct. */
+int dr_stencil5(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
+                dr_stream_t stream);
+
+/* The transposed operator A^T applied `steps` times (adjoint of dr_stencil5
+ * for the gradient w.r.t. the initial state).  With a zero ghost ring the
+ * operator is symmetric, so this runs the same update. */
+int dr_stencil5_T(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
+                  dr_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched execution: many independent segmented vectors in one launch        */
+/* ------------------------------------------------------------------------ */
+
+/* Plans y_v = inclusive_scan(x_v) and dots[v] = <x_v, p_v> (PLUS) for nvec
+ * independent fp32 vectors in ONE persistent launch.  x[v], p[v], y[v] are
+ * vectors of equal length (segmentations may differ); dev_dots has nvec fp32
+ * slots.  `tune` NULL = the default launch shape (see dr_batch_set_tune).  The
+ * plan allocates its device tables and workspace. */
+int dr_batch_plan(int nvec, const dr_vec* const* x, const dr_vec* const* p, dr_vec* const* y,
+                  float* dev_dots, const dr_tune* tune, dr_batch** out);
+int dr_batch_destroy(dr_batch* b);
+
+/* Changes the launch shape (invalidates a captured graph). */
+int dr_batch_set_tune(dr_batch* b, const dr_tune* tune);
+int dr_batch_get_tune(const dr_batch* b, dr_tune* tune);
+
+/* Runs the plan: one kernel launch, no allocation, no synchronization (safe to
+ * capture into a CUDA graph). */
+int dr_batch_run(dr_batch* b, dr_stream_t stream);
+
+/* Captures dr_batch_run into a CUDA graph once (on a private stream) and
+ * replays it on `stream`. */
+int dr_batch_run_graph(dr_batch* b, dr_stream_t stream);
+
+/* Baseline: the same work as one dr_inclusive_scan-kernel launch plus one
+ * transform_reduce-kernel launch per vector (2*nvec launches). */
+int dr_batch_run_per_range(dr_batch* b, dr_stream_t stream);
+
+/* Autotuner: times every candidate launch shape on the plan `calib` (its
+ * inputs must be initialized; its outputs are overwritten), picks the fastest
+ * and stores it in the JSON cache at cache_path (NULL = $DR_TUNE_CACHE, else
+ * no file), keyed by device name, SM count and a size bucket of the plan.
+ * mode 0: use a cached entry if present, else tune; mode 1: always re-tune.
+ * Writes the choice to *chosen and applies it to `calib`. */
+int dr_batch_autotune(dr_batch* calib, int mode, const char* cache_path, dr_tune* chosen);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DR_GB300_H */

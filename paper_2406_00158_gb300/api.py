@@ -1,0 +1,346 @@
+"""Thin Python layer over the C ABI: PyTorch supplies device memory and streams,
+every step of every algorithm runs in the library's CUDA kernels.
+
+Objects mirror the handles of ``dr.h``: ``SegmentedVector`` (dr_vec),
+``View`` (dr_view), ``MdArray`` (dr_md2), ``Batch`` (dr_batch).  Python
+objects keep references to the tensors and handles they were built from, so a
+view never outlives its base (Sec. 4.4: views are non-owning).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib as L
+from ._lib import call
+
+_DT = {torch.float32: L.DR_F32, torch.float64: L.DR_F64, torch.int64: L.DR_I64, torch.int32: L.DR_I32}
+_TORCH = {v: k for k, v in _DT.items()}
+_OPS = {"plus": L.DR_PLUS, "mul": L.DR_MUL, "min": L.DR_MIN, "max": L.DR_MAX}
+_UOPS = {"scale": L.DR_U_SCALE, "add": L.DR_U_ADD, "neg": L.DR_U_NEG, "abs": L.DR_U_ABS,
+         "square": L.DR_U_SQUARE}
+
+
+def _op(op) -> int:
+    return _OPS[op] if isinstance(op, str) else int(op)
+
+
+def stream_handle(stream: Optional[torch.cuda.Stream] = None) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _handle_out():
+    return ctypes.c_void_p()
+
+
+def _ptr_array(ptrs) -> ctypes.Array:
+    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
+
+
+def _scalar_bytes(value, dtype_code: int) -> ctypes.Array:
+    t = {L.DR_F32: ctypes.c_float, L.DR_F64: ctypes.c_double, L.DR_I64: ctypes.c_int64,
+         L.DR_I32: ctypes.c_int32}[dtype_code]
+    return t(value)
+
+
+def sync_status(stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Synchronizes the stream and raises DRError if a device-side wait expired."""
+    call("dr_sync_status", stream_handle(stream))
+
+
+def set_spin_limit(polls: int) -> None:
+    call("dr_set_spin_limit", int(polls))
+
+
+def debug_skip_publish(tile: int) -> None:
+    call("dr_debug_skip_publish", int(tile))
+
+
+def block_lengths(n: int, p: int) -> list[int]:
+    out = (ctypes.c_int64 * p)()
+    call("dr_block_lengths", int(n), int(p), out)
+    return list(out)
+
+
+class SegmentedVector:
+    """A distributed vector (Sec. 4.2.1) over caller-owned device segments."""
+
+    def __init__(self, segments: Sequence[torch.Tensor]):
+        segs = list(segments)
+        if not segs:
+            raise ValueError("a segmented vector needs at least one segment")
+        dt = segs[0].dtype
+        for s in segs:
+            if s.dtype != dt or s.dim() != 1 or not s.is_contiguous():
+                raise ValueError("segments must be 1-D contiguous tensors of one dtype")
+        self.segments = segs
+        self.dtype = dt
+        lens = (ctypes.c_int64 * len(segs))(*[s.numel() for s in segs])
+        ptrs = _ptr_array([s.data_ptr() for s in segs])
+        h = _handle_out()
+        call("dr_vec_create", _DT[dt], len(segs), lens, ptrs, ctypes.byref(h))
+        self.handle = h
+
+    @classmethod
+    def empty(cls, lens: Sequence[int], dtype=torch.float32, device="cuda"):
+        """One separate allocation per segment (one memory locale each)."""
+        return cls([torch.empty(int(n), dtype=dtype, device=device) for n in lens])
+
+    @classmethod
+    def from_tensor(cls, t: torch.Tensor, lens: Sequence[int]):
+        """Copies a flat tensor into a new vector with the given segment sizes."""
+        v = cls.empty(lens, t.dtype, t.device)
+        off = 0
+        for s in v.segments:
+            s.copy_(t[off:off + s.numel()])
+            off += s.numel()
+        return v
+
+    @property
+    def n(self) -> int:
+        return sum(s.numel() for s in self.segments)
+
+    @property
+    def lens(self) -> list[int]:
+        return [s.numel() for s in self.segments]
+
+    def locate(self, i: int) -> tuple[int, int]:
+        seg, off = ctypes.c_int(), ctypes.c_int64()
+        call("dr_vec_locate", self.handle, int(i), ctypes.byref(seg), ctypes.byref(off))
+        return seg.value, off.value
+
+    def to_tensor(self) -> torch.Tensor:
+        return torch.cat(self.segments) if self.segments else torch.empty(0)
+
+    def copy_from_host(self, host: torch.Tensor, stream=None) -> None:
+        assert host.device.type == "cpu" and host.is_contiguous() and host.numel() == self.n
+        call("dr_vec_copy_from_host", self.handle, ctypes.c_void_p(host.data_ptr()), stream_handle(stream))
+
+    def copy_to_host(self, host: torch.Tensor, stream=None) -> None:
+        assert host.device.type == "cpu" and host.is_contiguous() and host.numel() == self.n
+        call("dr_vec_copy_to_host", self.handle, ctypes.c_void_p(host.data_ptr()), stream_handle(stream))
+
+    def view(self) -> "View":
+        return View.of(self)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.dr_vec_destroy(h)
+
+
+class View:
+    """A lazy view (Sec. 4.4); its kernels fuse it into their loads."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    @classmethod
+    def of(cls, v: SegmentedVector) -> "View":
+        h = _handle_out()
+        call("dr_view_of", v.handle, ctypes.byref(h))
+        return cls(h, [v])
+
+    def transform(self, op, arg: float = 0.0) -> "View":
+        h = _handle_out()
+        call("dr_view_transform", self.handle, _UOPS[op] if isinstance(op, str) else int(op), float(arg),
+             ctypes.byref(h))
+        return View(h, [self])
+
+    def zip(self, other: "View") -> "View":
+        h = _handle_out()
+        call("dr_view_zip", self.handle, other.handle, ctypes.byref(h))
+        return View(h, [self, other])
+
+    def zip_transform(self, op) -> "View":
+        h = _handle_out()
+        call("dr_view_zip_transform", self.handle, _op(op), ctypes.byref(h))
+        return View(h, [self])
+
+    def take(self, l: int) -> "View":
+        h = _handle_out()
+        call("dr_view_take", self.handle, int(l), ctypes.byref(h))
+        return View(h, [self])
+
+    def drop(self, f: int) -> "View":
+        h = _handle_out()
+        call("dr_view_drop", self.handle, int(f), ctypes.byref(h))
+        return View(h, [self])
+
+    def info(self) -> dict:
+        size, arity, dtype, np_ = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        call("dr_view_info", self.handle, ctypes.byref(size), ctypes.byref(arity), ctypes.byref(dtype),
+             ctypes.byref(np_))
+        return {"size": size.value, "arity": arity.value, "dtype": dtype.value, "npieces": np_.value}
+
+    @property
+    def size(self) -> int:
+        return self.info()["size"]
+
+    def segments(self) -> list[tuple]:
+        """(start, len, seg_a, off_a, seg_b, off_b) per piece of the segmentation."""
+        n = self.info()["npieces"]
+        arr = (L.dr_piece * max(1, n))()
+        call("dr_view_segments", self.handle, n, arr)
+        return [(p.start, p.len, p.seg[0], p.off[0], p.seg[1], p.off[1]) for p in arr[:n]]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.dr_view_destroy(h)
+
+
+def _as_view(v) -> View:
+    return v if isinstance(v, View) else View.of(v)
+
+
+def dot_view(x: SegmentedVector, y: SegmentedVector) -> View:
+    """zip(x, y) | transform(multiply): the view of Algorithm 1."""
+    return View.of(x).zip(View.of(y)).zip_transform("mul")
+
+
+def inclusive_scan(inp, out: SegmentedVector, op="plus", stream=None) -> SegmentedVector:
+    call("dr_inclusive_scan", _as_view(inp).handle, out.handle, _op(op), stream_handle(stream))
+    return out
+
+
+def exclusive_scan(inp, out: SegmentedVector, init, op="plus", stream=None) -> SegmentedVector:
+    v = _as_view(inp)
+    init_c = _scalar_bytes(init, _DT[out.dtype])
+    call("dr_exclusive_scan", v.handle, out.handle, _op(op), ctypes.byref(init_c), stream_handle(stream))
+    return out
+
+
+def reverse_inclusive_scan(inp, out: SegmentedVector, stream=None) -> SegmentedVector:
+    call("dr_reverse_inclusive_scan", _as_view(inp).handle, out.handle, stream_handle(stream))
+    return out
+
+
+def transform_reduce(inp, out: torch.Tensor, op="plus", init=0, stream=None) -> torch.Tensor:
+    """out[0] = init op v_0 op ... op v_{n-1}; `out` is a 1-element device tensor."""
+    v = _as_view(inp)
+    init_c = _scalar_bytes(init, _DT[out.dtype])
+    call("dr_transform_reduce", v.handle, _op(op), ctypes.byref(init_c), ctypes.c_void_p(out.data_ptr()),
+         stream_handle(stream))
+    return out
+
+
+def scale_by_partner(x: SegmentedVector, y: SegmentedVector, g: torch.Tensor, gx: Optional[SegmentedVector],
+                     gy: Optional[SegmentedVector], stream=None) -> None:
+    call("dr_scale_by_partner", x.handle, y.handle, ctypes.c_void_p(g.data_ptr()),
+         gx.handle if gx is not None else None, gy.handle if gy is not None else None, stream_handle(stream))
+
+
+class MdArray:
+    """Row-block segmented 2-D fp32 array with one ghost row above and below
+    each block (block k: tensor of shape (rows_k + 2, cols))."""
+
+    def __init__(self, blocks: Sequence[torch.Tensor]):
+        blocks = list(blocks)
+        cols = blocks[0].shape[1]
+        for b in blocks:
+            if b.dtype != torch.float32 or b.dim() != 2 or b.shape[1] != cols or not b.is_contiguous():
+                raise ValueError("blocks must be contiguous fp32 (rows_k + 2, cols) tensors")
+        self.blocks = blocks
+        self.cols = cols
+        self.seg_rows = [b.shape[0] - 2 for b in blocks]
+        self.rows = sum(self.seg_rows)
+        srows = (ctypes.c_int64 * len(blocks))(*self.seg_rows)
+        h = _handle_out()
+        call("dr_md2_create", L.DR_F32, self.rows, cols, len(blocks), srows,
+             _ptr_array([b.data_ptr() for b in blocks]), ctypes.byref(h))
+        self.handle = h
+
+    @classmethod
+    def empty(cls, seg_rows: Sequence[int], cols: int, device="cuda"):
+        return cls([torch.zeros(int(r) + 2, cols, dtype=torch.float32, device=device) for r in seg_rows])
+
+    @classmethod
+    def from_tensor(cls, u: torch.Tensor, seg_rows: Sequence[int]):
+        m = cls.empty(seg_rows, u.shape[1], u.device)
+        m.load(u)
+        return m
+
+    def load(self, u: torch.Tensor) -> None:
+        r = 0
+        for b, k in zip(self.blocks, self.seg_rows):
+            b[1:k + 1].copy_(u[r:r + k])
+            r += k
+
+    def to_tensor(self) -> torch.Tensor:
+        return torch.cat([b[1:k + 1] for b, k in zip(self.blocks, self.seg_rows)])
+
+    def exchange_halos(self, stream=None) -> None:
+        call("dr_md2_exchange_halos", self.handle, stream_handle(stream))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.dr_md2_destroy(h)
+
+
+def stencil5(inp: MdArray, out: MdArray, tmp: Optional[MdArray], steps: int, wc: float = 0.0,
+             wn: float = 0.25, stream=None) -> MdArray:
+    call("dr_stencil5", inp.handle, out.handle, tmp.handle if tmp is not None else None, int(steps),
+         float(wc), float(wn), stream_handle(stream))
+    return out
+
+
+def stencil5_T(inp: MdArray, out: MdArray, tmp: Optional[MdArray], steps: int, wc: float = 0.0,
+               wn: float = 0.25, stream=None) -> MdArray:
+    call("dr_stencil5_T", inp.handle, out.handle, tmp.handle if tmp is not None else None, int(steps),
+         float(wc), float(wn), stream_handle(stream))
+    return out
+
+
+class Batch:
+    """y_v = inclusive_scan(x_v), dots[v] = <x_v, p_v> for many vectors in one launch."""
+
+    def __init__(self, xs: Sequence[SegmentedVector], ps: Sequence[SegmentedVector],
+                 ys: Sequence[SegmentedVector], dots: torch.Tensor, tune: Optional[tuple] = None):
+        n = len(xs)
+        assert len(ps) == n and len(ys) == n and dots.numel() >= n and dots.dtype == torch.float32
+        self._keep = (list(xs), list(ps), list(ys), dots)
+        arr = lambda vs: (ctypes.c_void_p * n)(*[v.handle.value for v in vs])
+        t = L.dr_tune(*tune) if tune else None
+        h = _handle_out()
+        call("dr_batch_plan", n, arr(xs), arr(ps), arr(ys), ctypes.c_void_p(dots.data_ptr()),
+             ctypes.byref(t) if t is not None else None, ctypes.byref(h))
+        self.handle = h
+        self.nvec = n
+
+    def run(self, stream=None) -> None:
+        call("dr_batch_run", self.handle, stream_handle(stream))
+
+    def run_graph(self, stream=None) -> None:
+        call("dr_batch_run_graph", self.handle, stream_handle(stream))
+
+    def run_per_range(self, stream=None) -> None:
+        call("dr_batch_run_per_range", self.handle, stream_handle(stream))
+
+    @property
+    def tune(self) -> tuple:
+        t = L.dr_tune()
+        call("dr_batch_get_tune", self.handle, ctypes.byref(t))
+        return (t.threads, t.items, t.ctas_per_sm)
+
+    @tune.setter
+    def tune(self, value) -> None:
+        t = L.dr_tune(*value)
+        call("dr_batch_set_tune", self.handle, ctypes.byref(t))
+
+    def autotune(self, retune: bool = False, cache_path: Optional[str] = None) -> tuple:
+        t = L.dr_tune()
+        call("dr_batch_autotune", self.handle, 1 if retune else 0,
+             cache_path.encode() if cache_path else None, ctypes.byref(t))
+        return (t.threads, t.items, t.ctas_per_sm)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and L._lib is not None:
+            L._lib.dr_batch_destroy(h)

@@ -1,0 +1,767 @@
+// Host side of the C ABI (dr.h): handles, view composition and flattening,
+// re-segmentation, argument validation, and the algorithm entry points that
+// fill kernel parameters and launch.  No entry point throws or aborts.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "dr_host.h"
+
+namespace dr {
+
+// ---------------------------------------------------------------------------
+// errors, per-device status word, knobs
+// ---------------------------------------------------------------------------
+static thread_local std::string t_msg;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_msg = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(DR_E_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { t_msg.clear(); }
+
+int esize(int dtype) {
+  switch (dtype) {
+    case DR_F32:
+    case DR_I32: return 4;
+    case DR_F64:
+    case DR_I64: return 8;
+    default: return 0;
+  }
+}
+
+bool valid_dtype(int dtype) { return esize(dtype) != 0; }
+
+// [0] = first failure code, [1] = its info (tile / item index)
+__device__ unsigned g_status[4];
+
+static std::mutex g_mu;
+static constexpr int kMaxDevices = 64;
+static unsigned* g_status_addr[kMaxDevices];
+static std::atomic<int64_t> g_spin{int64_t(1) << 21};
+static std::atomic<int64_t> g_skip{-1};
+
+unsigned* status_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_status_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    g_status_addr[dev] = static_cast<unsigned*>(p);
+  }
+  return g_status_addr[dev];
+}
+
+int64_t spin_limit() { return g_spin.load(); }
+int64_t take_skip_publish() { return g_skip.exchange(-1); }
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+int Workspace::ensure(size_t need, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (ptr && bytes >= need && device == dev) return DR_OK;
+  if (ptr) {
+    // the old workspace may still be in use by work queued on `s`
+    cudaStreamSynchronize(s);
+    release();
+  }
+  need = (need + 255) / 256 * 256;
+  e = cudaMalloc(&ptr, need);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    return fail(DR_E_NOMEM, "workspace allocation of %zu bytes failed: %s", need, cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(ptr, 0, need, s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
+  bytes = need;
+  device = dev;
+  return DR_OK;
+}
+
+void Workspace::release() {
+  if (ptr) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != device) cudaSetDevice(device);
+    cudaDeviceSynchronize();  // kernels queued on any stream may still use it
+    cudaFree(ptr);
+    if (cur != device) cudaSetDevice(cur);
+  }
+  ptr = nullptr;
+  bytes = 0;
+  device = -1;
+}
+
+// ---------------------------------------------------------------------------
+// re-segmentation (Sec. 4.4 "Zip")
+// ---------------------------------------------------------------------------
+std::vector<Piece> resegment(const std::vector<std::vector<Seg>>& ops, int esz) {
+  const size_t k = ops.size();
+  std::vector<Piece> out;
+  std::vector<size_t> si(k, 0);
+  std::vector<int64_t> used(k, 0);
+  int64_t pos = 0;
+  while (true) {
+    bool done = false;
+    for (size_t o = 0; o < k; ++o) {
+      while (si[o] < ops[o].size() && used[o] >= ops[o][si[o]].len) {
+        ++si[o];
+        used[o] = 0;
+      }
+      if (si[o] == ops[o].size()) done = true;
+    }
+    if (done || k == 0) break;
+    int64_t take = INT64_MAX;
+    for (size_t o = 0; o < k; ++o) take = std::min(take, ops[o][si[o]].len - used[o]);
+    Piece pc{};
+    pc.start = pos;
+    pc.len = take;
+    for (size_t o = 0; o < k; ++o) {
+      const Seg& s = ops[o][si[o]];
+      pc.p[o] = s.p + used[o] * esz;
+      pc.seg[o] = s.idx;
+      pc.off[o] = s.off + used[o];
+      used[o] += take;
+    }
+    out.push_back(pc);
+    pos += take;
+  }
+  return out;
+}
+
+}  // namespace dr
+
+using namespace dr;
+
+std::vector<Seg> dr_vec::window(int64_t lo, int64_t hi) const {
+  std::vector<Seg> out;
+  for (size_t k = 0; k < ptr.size(); ++k) {
+    const int64_t a = std::max(lo, start[k]), b = std::min(hi, start[k] + len[k]);
+    if (b > a) out.push_back(Seg{ptr[k] + (a - start[k]) * esz, b - a, (int32_t)k, a - start[k]});
+  }
+  return out;
+}
+
+void dr_view::recompute() {
+  std::vector<std::vector<Seg>> ops;
+  size = INT64_MAX;
+  for (int l = 0; l < nleaf; ++l) {
+    ops.push_back(leaf[l].vec->window(leaf[l].lo, leaf[l].hi));
+    size = std::min(size, leaf[l].hi - leaf[l].lo);
+  }
+  if (size < 0) size = 0;
+  pieces = resegment(ops, esize(dtype));
+}
+
+KViewCode dr_view::code() const {
+  KViewCode c{};
+  c.nleaf = nleaf;
+  c.zipop = zipop < 0 ? DR_PLUS : zipop;
+  c.npost = npost;
+  for (int l = 0; l < 2; ++l) {
+    c.npre[l] = npre[l];
+    for (int k = 0; k < kMaxChain; ++k) {
+      c.pre_op[l][k] = pre_op[l][k];
+      c.pre_arg[l][k] = pre_arg[l][k];
+    }
+  }
+  for (int k = 0; k < kMaxChain; ++k) {
+    c.post_op[k] = post_op[k];
+    c.post_arg[k] = post_arg[k];
+  }
+  if (nleaf == 1 && npre[0] == 0 && npost == 0) c.kind = 0;
+  else if (nleaf == 2 && zipop == DR_MUL && npre[0] == 0 && npre[1] == 0 && npost == 0) c.kind = 1;
+  else c.kind = 2;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// status
+// ---------------------------------------------------------------------------
+extern "C" const char* dr_last_error(void) { return t_msg.c_str(); }
+
+extern "C" int dr_version(void) { return 1; }
+
+extern "C" int dr_sync_status(dr_stream_t stream) {
+  clear_error();
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  unsigned h[4] = {0, 0, 0, 0};
+  e = cudaMemcpyFromSymbol(h, g_status, sizeof h);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+  if (h[0] != 0) {
+    const unsigned z[4] = {0, 0, 0, 0};
+    cudaMemcpyToSymbol(g_status, z, sizeof z);
+    if (h[0] == DR_E_TIMEOUT)
+      return fail(DR_E_TIMEOUT, "a bounded device wait expired (tile/item %u); results of the kernels "
+                                "launched since the last check are invalid", h[1]);
+    return fail((int)h[0], "device reported status %u (info %u)", h[0], h[1]);
+  }
+  return DR_OK;
+}
+
+extern "C" int dr_set_spin_limit(int64_t polls) {
+  clear_error();
+  if (polls < 1) return fail(DR_E_INVAL, "spin limit must be >= 1 (got %lld)", (long long)polls);
+  g_spin.store(polls);
+  return DR_OK;
+}
+
+extern "C" int dr_debug_skip_publish(int64_t tile) {
+  clear_error();
+  g_skip.store(tile < 0 ? -1 : tile);
+  return DR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// segmented vector
+// ---------------------------------------------------------------------------
+extern "C" int dr_block_lengths(int64_t n, int p, int64_t* lens_out) {
+  clear_error();
+  if (n < 0 || p < 1 || !lens_out) return fail(DR_E_INVAL, "dr_block_lengths: need n >= 0, p >= 1, lens_out");
+  const int64_t b = (n + p - 1) / p;
+  int64_t left = n;
+  for (int k = 0; k < p; ++k) {
+    lens_out[k] = std::min(b, left);
+    left -= lens_out[k];
+  }
+  return DR_OK;
+}
+
+extern "C" int dr_vec_create(int dtype, int nseg, const int64_t* lens, void* const* seg_ptrs,
+                             dr_vec** out) {
+  clear_error();
+  if (!out) return fail(DR_E_INVAL, "dr_vec_create: out is NULL");
+  *out = nullptr;
+  if (!valid_dtype(dtype)) return fail(DR_E_DTYPE, "dr_vec_create: unknown dtype %d", dtype);
+  if (nseg < 1 || !lens || !seg_ptrs) return fail(DR_E_INVAL, "dr_vec_create: need nseg >= 1, lens, seg_ptrs");
+  const int esz = esize(dtype);
+  for (int k = 0; k < nseg; ++k) {
+    if (lens[k] < 0) return fail(DR_E_INVAL, "dr_vec_create: segment %d has negative length", k);
+    if (lens[k] > 0 && !seg_ptrs[k]) return fail(DR_E_INVAL, "dr_vec_create: segment %d pointer is NULL", k);
+    if ((uintptr_t)seg_ptrs[k] % esz)
+      return fail(DR_E_ALIGN, "dr_vec_create: segment %d pointer not aligned to %d bytes", k, esz);
+  }
+  dr_vec* v = new (std::nothrow) dr_vec();
+  if (!v) return fail(DR_E_NOMEM, "dr_vec_create: out of host memory");
+  v->dtype = dtype;
+  v->esz = esz;
+  int64_t s = 0;
+  for (int k = 0; k < nseg; ++k) {
+    v->ptr.push_back(static_cast<char*>(seg_ptrs[k]));
+    v->len.push_back(lens[k]);
+    v->start.push_back(s);
+    s += lens[k];
+  }
+  v->n = s;
+  *out = v;
+  return DR_OK;
+}
+
+extern "C" int dr_vec_destroy(dr_vec* v) {
+  clear_error();
+  delete v;
+  return DR_OK;
+}
+
+extern "C" int dr_vec_info(const dr_vec* v, int* dtype, int* nseg, int64_t* n) {
+  clear_error();
+  if (!v) return fail(DR_E_INVAL, "dr_vec_info: NULL vector");
+  if (dtype) *dtype = v->dtype;
+  if (nseg) *nseg = (int)v->ptr.size();
+  if (n) *n = v->n;
+  return DR_OK;
+}
+
+extern "C" int dr_vec_segment(const dr_vec* v, int k, void** ptr, int64_t* len, int64_t* start) {
+  clear_error();
+  if (!v) return fail(DR_E_INVAL, "dr_vec_segment: NULL vector");
+  if (k < 0 || k >= (int)v->ptr.size()) return fail(DR_E_BOUNDS, "dr_vec_segment: no segment %d", k);
+  if (ptr) *ptr = v->ptr[k];
+  if (len) *len = v->len[k];
+  if (start) *start = v->start[k];
+  return DR_OK;
+}
+
+extern "C" int dr_vec_locate(const dr_vec* v, int64_t i, int* seg, int64_t* off) {
+  clear_error();
+  if (!v) return fail(DR_E_INVAL, "dr_vec_locate: NULL vector");
+  if (i < 0 || i >= v->n) return fail(DR_E_BOUNDS, "dr_vec_locate: index %lld outside [0, %lld)", (long long)i, (long long)v->n);
+  // last segment whose start is <= i; empty segments share starts, step back over them
+  auto it = std::upper_bound(v->start.begin(), v->start.end(), i);
+  int k = (int)(it - v->start.begin()) - 1;
+  while (k > 0 && (v->len[k] == 0 || i >= v->start[k] + v->len[k])) --k;
+  if (seg) *seg = k;
+  if (off) *off = i - v->start[k];
+  return DR_OK;
+}
+
+static int copy_vec(const dr_vec* v, void* host, bool to_host, cudaStream_t s) {
+  for (size_t k = 0; k < v->ptr.size(); ++k) {
+    if (!v->len[k]) continue;
+    char* h = static_cast<char*>(host) + v->start[k] * v->esz;
+    cudaError_t e = to_host ? cudaMemcpyAsync(h, v->ptr[k], v->len[k] * v->esz, cudaMemcpyDeviceToHost, s)
+                            : cudaMemcpyAsync(v->ptr[k], h, v->len[k] * v->esz, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, to_host ? "copy segment to host" : "copy segment from host");
+  }
+  return DR_OK;
+}
+
+extern "C" int dr_vec_copy_from_host(dr_vec* v, const void* host, dr_stream_t stream) {
+  clear_error();
+  if (!v || (!host && v->n)) return fail(DR_E_INVAL, "dr_vec_copy_from_host: NULL argument");
+  return copy_vec(v, const_cast<void*>(host), false, (cudaStream_t)stream);
+}
+
+extern "C" int dr_vec_copy_to_host(const dr_vec* v, void* host, dr_stream_t stream) {
+  clear_error();
+  if (!v || (!host && v->n)) return fail(DR_E_INVAL, "dr_vec_copy_to_host: NULL argument");
+  return copy_vec(v, host, true, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// row-block 2-D array
+// ---------------------------------------------------------------------------
+extern "C" int dr_md2_create(int dtype, int64_t rows, int64_t cols, int nseg, const int64_t* seg_rows,
+                             void* const* seg_ptrs, dr_md2** out) {
+  clear_error();
+  if (!out) return fail(DR_E_INVAL, "dr_md2_create: out is NULL");
+  *out = nullptr;
+  if (dtype != DR_F32) return fail(DR_E_DTYPE, "dr_md2_create: only DR_F32 is supported");
+  if (rows < 1 || cols < 1 || nseg < 1 || nseg > kMaxPieces || !seg_rows || !seg_ptrs)
+    return fail(DR_E_INVAL, "dr_md2_create: need rows, cols >= 1, 1 <= nseg <= %d, seg_rows, seg_ptrs", kMaxPieces);
+  int64_t sum = 0;
+  for (int k = 0; k < nseg; ++k) {
+    if (seg_rows[k] < 1) return fail(DR_E_INVAL, "dr_md2_create: block %d has %lld rows", k, (long long)seg_rows[k]);
+    if (!seg_ptrs[k]) return fail(DR_E_INVAL, "dr_md2_create: block %d pointer is NULL", k);
+    if ((uintptr_t)seg_ptrs[k] % 4) return fail(DR_E_ALIGN, "dr_md2_create: block %d pointer not 4-byte aligned", k);
+    sum += seg_rows[k];
+  }
+  if (sum != rows) return fail(DR_E_INVAL, "dr_md2_create: block rows sum to %lld, not %lld", (long long)sum, (long long)rows);
+  dr_md2* m = new (std::nothrow) dr_md2();
+  if (!m) return fail(DR_E_NOMEM, "dr_md2_create: out of host memory");
+  m->dtype = dtype;
+  m->rows = rows;
+  m->cols = cols;
+  for (int k = 0; k < nseg; ++k) {
+    m->ptr.push_back(static_cast<char*>(seg_ptrs[k]));
+    m->srows.push_back(seg_rows[k]);
+  }
+  *out = m;
+  return DR_OK;
+}
+
+extern "C" int dr_md2_destroy(dr_md2* m) {
+  clear_error();
+  delete m;
+  return DR_OK;
+}
+
+static int exchange_halos(const dr_md2* m, cudaStream_t s) {
+  if (m->ptr.size() < 2) return DR_OK;
+  HaloParams p{};
+  p.nbound = (int)m->ptr.size() - 1;
+  p.cols = m->cols;
+  for (int k = 0; k < p.nbound; ++k) {
+    float* a = reinterpret_cast<float*>(m->ptr[k]);
+    float* b = reinterpret_cast<float*>(m->ptr[k + 1]);
+    p.b[k].src_last = a + m->srows[k] * m->cols;
+    p.b[k].dst_top_ghost = b;
+    p.b[k].src_first = b + m->cols;
+    p.b[k].dst_bot_ghost = a + (m->srows[k] + 1) * m->cols;
+  }
+  cudaError_t e = launch_halo(p, s);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, "halo exchange launch");
+}
+
+extern "C" int dr_md2_exchange_halos(dr_md2* m, dr_stream_t stream) {
+  clear_error();
+  if (!m) return fail(DR_E_INVAL, "dr_md2_exchange_halos: NULL array");
+  return exchange_halos(m, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// views
+// ---------------------------------------------------------------------------
+extern "C" int dr_view_of(const dr_vec* v, dr_view** out) {
+  clear_error();
+  if (!v || !out) return fail(DR_E_INVAL, "dr_view_of: NULL argument");
+  dr_view* w = new (std::nothrow) dr_view();
+  if (!w) return fail(DR_E_NOMEM, "dr_view_of: out of host memory");
+  w->dtype = v->dtype;
+  w->arity = 1;
+  w->nleaf = 1;
+  w->leaf[0] = {v, 0, v->n};
+  w->recompute();
+  *out = w;
+  return DR_OK;
+}
+
+static dr_view* clone_view(const dr_view* b) {
+  dr_view* w = new (std::nothrow) dr_view();
+  if (!w) return nullptr;
+  w->dtype = b->dtype;
+  w->arity = b->arity;
+  w->nleaf = b->nleaf;
+  w->leaf[0] = b->leaf[0];
+  w->leaf[1] = b->leaf[1];
+  std::memcpy(w->npre, b->npre, sizeof w->npre);
+  std::memcpy(w->pre_op, b->pre_op, sizeof w->pre_op);
+  std::memcpy(w->pre_arg, b->pre_arg, sizeof w->pre_arg);
+  w->zipop = b->zipop;
+  w->npost = b->npost;
+  std::memcpy(w->post_op, b->post_op, sizeof w->post_op);
+  std::memcpy(w->post_arg, b->post_arg, sizeof w->post_arg);
+  w->size = b->size;
+  w->pieces = b->pieces;
+  return w;
+}
+
+extern "C" int dr_view_transform(const dr_view* base, int op, double arg, dr_view** out) {
+  clear_error();
+  if (!base || !out) return fail(DR_E_INVAL, "dr_view_transform: NULL argument");
+  if (base->arity != 1)
+    return fail(DR_E_INVAL, "dr_view_transform: base is a raw zip; use dr_view_zip_transform first");
+  if (op < DR_U_SCALE || op > DR_U_SQUARE) return fail(DR_E_INVAL, "dr_view_transform: unknown op %d", op);
+  if (base->npost >= kMaxChain)
+    return fail(DR_E_UNSUPPORTED, "dr_view_transform: more than %d chained transforms", kMaxChain);
+  dr_view* w = clone_view(base);
+  if (!w) return fail(DR_E_NOMEM, "dr_view_transform: out of host memory");
+  w->post_op[w->npost] = op;
+  w->post_arg[w->npost] = arg;
+  w->npost++;
+  *out = w;
+  return DR_OK;
+}
+
+extern "C" int dr_view_zip(const dr_view* a, const dr_view* b, dr_view** out) {
+  clear_error();
+  if (!a || !b || !out) return fail(DR_E_INVAL, "dr_view_zip: NULL argument");
+  if (a->arity != 1 || b->arity != 1 || a->nleaf != 1 || b->nleaf != 1)
+    return fail(DR_E_UNSUPPORTED, "dr_view_zip: operands must be (transformed) views of one vector each");
+  if (a->dtype != b->dtype) return fail(DR_E_DTYPE, "dr_view_zip: operand dtypes differ");
+  dr_view* w = new (std::nothrow) dr_view();
+  if (!w) return fail(DR_E_NOMEM, "dr_view_zip: out of host memory");
+  w->dtype = a->dtype;
+  w->arity = 2;
+  w->nleaf = 2;
+  w->leaf[0] = a->leaf[0];
+  w->leaf[1] = b->leaf[0];
+  w->npre[0] = a->npost;
+  w->npre[1] = b->npost;
+  for (int k = 0; k < kMaxChain; ++k) {
+    w->pre_op[0][k] = a->post_op[k];
+    w->pre_arg[0][k] = a->post_arg[k];
+    w->pre_op[1][k] = b->post_op[k];
+    w->pre_arg[1][k] = b->post_arg[k];
+  }
+  w->recompute();
+  *out = w;
+  return DR_OK;
+}
+
+extern "C" int dr_view_zip_transform(const dr_view* zip, int op, dr_view** out) {
+  clear_error();
+  if (!zip || !out) return fail(DR_E_INVAL, "dr_view_zip_transform: NULL argument");
+  if (zip->arity != 2) return fail(DR_E_INVAL, "dr_view_zip_transform: base is not a zip");
+  if (op < DR_PLUS || op > DR_MAX) return fail(DR_E_INVAL, "dr_view_zip_transform: unknown op %d", op);
+  dr_view* w = clone_view(zip);
+  if (!w) return fail(DR_E_NOMEM, "dr_view_zip_transform: out of host memory");
+  w->arity = 1;
+  w->zipop = op;
+  *out = w;
+  return DR_OK;
+}
+
+static int trim(const dr_view* base, int64_t lo_add, int64_t new_size, dr_view** out) {
+  dr_view* w = clone_view(base);
+  if (!w) return fail(DR_E_NOMEM, "take/drop: out of host memory");
+  for (int l = 0; l < w->nleaf; ++l) {
+    w->leaf[l].lo += lo_add;
+    w->leaf[l].hi = std::min(w->leaf[l].hi, w->leaf[l].lo + new_size);
+  }
+  w->recompute();
+  *out = w;
+  return DR_OK;
+}
+
+extern "C" int dr_view_take(const dr_view* base, int64_t l, dr_view** out) {
+  clear_error();
+  if (!base || !out) return fail(DR_E_INVAL, "dr_view_take: NULL argument");
+  l = std::max<int64_t>(0, std::min(l, base->size));
+  return trim(base, 0, l, out);
+}
+
+extern "C" int dr_view_drop(const dr_view* base, int64_t f, dr_view** out) {
+  clear_error();
+  if (!base || !out) return fail(DR_E_INVAL, "dr_view_drop: NULL argument");
+  f = std::max<int64_t>(0, std::min(f, base->size));
+  return trim(base, f, base->size - f, out);
+}
+
+extern "C" int dr_view_destroy(dr_view* v) {
+  clear_error();
+  if (v) {
+    v->ws_scan.release();
+    v->ws_reduce.release();
+  }
+  delete v;
+  return DR_OK;
+}
+
+extern "C" int dr_view_info(const dr_view* v, int64_t* size, int* arity, int* dtype, int* npieces) {
+  clear_error();
+  if (!v) return fail(DR_E_INVAL, "dr_view_info: NULL view");
+  if (size) *size = v->size;
+  if (arity) *arity = v->arity;
+  if (dtype) *dtype = v->dtype;
+  if (npieces) *npieces = (int)v->pieces.size();
+  return DR_OK;
+}
+
+extern "C" int dr_view_segments(const dr_view* v, int max_pieces, dr_piece* out) {
+  clear_error();
+  if (!v || (!out && max_pieces > 0)) return fail(DR_E_INVAL, "dr_view_segments: NULL argument");
+  const int n = std::min<int>(max_pieces, (int)v->pieces.size());
+  for (int i = 0; i < n; ++i) {
+    const Piece& p = v->pieces[i];
+    out[i].start = p.start;
+    out[i].len = p.len;
+    for (int l = 0; l < 2; ++l) {
+      out[i].seg[l] = l < v->nleaf ? p.seg[l] : -1;
+      out[i].off[l] = l < v->nleaf ? p.off[l] : 0;
+    }
+  }
+  return DR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// algorithms
+// ---------------------------------------------------------------------------
+
+// The pieces of a call: the view's leaves (and the output, if any) re-segmented
+// together, each cut into tiles of `tile` elements.
+static int call_pieces(const dr_view* in, const dr_vec* out, int tile, KPiece* pc, int* npieces,
+                       int64_t* ntiles) {
+  std::vector<std::vector<Seg>> ops;
+  for (int l = 0; l < in->nleaf; ++l) ops.push_back(in->leaf[l].vec->window(in->leaf[l].lo, in->leaf[l].hi));
+  if (out) ops.push_back(out->window(0, in->size));
+  const std::vector<Piece> ps = resegment(ops, esize(in->dtype));
+  if ((int)ps.size() > kMaxPieces)
+    return fail(DR_E_UNSUPPORTED, "call spans %zu segments after re-segmentation (limit %d)", ps.size(), kMaxPieces);
+  int64_t t = 0;
+  for (size_t i = 0; i < ps.size(); ++i) {
+    KPiece& k = pc[i];
+    k.a = ps[i].p[0];
+    k.b = in->nleaf == 2 ? ps[i].p[1] : nullptr;
+    k.o = out ? ps[i].p[in->nleaf] : nullptr;
+    k.len = ps[i].len;
+    k.tile_begin = t;
+    k.vec_ok = ((uintptr_t)k.a % 16 == 0) && ((uintptr_t)k.b % 16 == 0) && ((uintptr_t)k.o % 16 == 0);
+    t += (ps[i].len + tile - 1) / tile;
+  }
+  *npieces = (int)ps.size();
+  *ntiles = t;
+  return DR_OK;
+}
+
+static int check_single(const dr_view* in, const char* who) {
+  if (!in) return fail(DR_E_INVAL, "%s: NULL input view", who);
+  if (in->arity != 1) return fail(DR_E_INVAL, "%s: input is a raw zip; apply dr_view_zip_transform", who);
+  return DR_OK;
+}
+
+static int do_scan(const char* who, const dr_view* in_c, dr_vec* out, int op, bool reverse, bool exclusive,
+                   const void* init, cudaStream_t s) {
+  clear_error();
+  if (int r = check_single(in_c, who)) return r;
+  dr_view* in = const_cast<dr_view*>(in_c);
+  if (!out) return fail(DR_E_INVAL, "%s: NULL output", who);
+  if (out->dtype != in->dtype) return fail(DR_E_DTYPE, "%s: output dtype differs from input", who);
+  if (out->n < in->size)
+    return fail(DR_E_INVAL, "%s: output has %lld elements, input %lld", who, (long long)out->n, (long long)in->size);
+  if (op != DR_PLUS && op != DR_MIN && op != DR_MAX) return fail(DR_E_INVAL, "%s: op must be PLUS, MIN or MAX", who);
+  if (exclusive && !init) return fail(DR_E_INVAL, "%s: NULL init", who);
+  if (in->size == 0) return DR_OK;
+  static thread_local ScanParams p;
+  std::memset(&p, 0, sizeof p);
+  p.vc = in->code();
+  p.op = op;
+  p.dtype = in->dtype;
+  p.exclusive = exclusive ? 1 : 0;
+  if (int r = call_pieces(in, out, scan_tile_elems(in->dtype), p.pc, &p.npieces, &p.ntiles)) return r;
+  if (int r = in->ws_scan.ensure(scan_ws_bytes(p.ntiles, in->dtype), s)) return r;
+  p.ws = static_cast<char*>(in->ws_scan.ptr);
+  p.status = status_word();
+  if (!p.status) return fail(DR_E_CUDA, "%s: no device status word", who);
+  p.spin_limit = spin_limit();
+  p.skip_tile = take_skip_publish();
+  if (exclusive) std::memcpy(&p.init_bits, init, esize(in->dtype));
+  cudaError_t e = launch_scan(p, reverse, scan_grid(in->dtype, p.ntiles), s);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
+}
+
+extern "C" int dr_inclusive_scan(const dr_view* in, dr_vec* out, int op, dr_stream_t stream) {
+  return do_scan("dr_inclusive_scan", in, out, op, false, false, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int dr_exclusive_scan(const dr_view* in, dr_vec* out, int op, const void* init, dr_stream_t stream) {
+  return do_scan("dr_exclusive_scan", in, out, op, false, true, init, (cudaStream_t)stream);
+}
+
+extern "C" int dr_reverse_inclusive_scan(const dr_view* in, dr_vec* out, dr_stream_t stream) {
+  return do_scan("dr_reverse_inclusive_scan", in, out, DR_PLUS, true, false, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int dr_transform_reduce(const dr_view* in_c, int op, const void* init, void* dev_result,
+                                   dr_stream_t stream) {
+  clear_error();
+  const char* who = "dr_transform_reduce";
+  if (int r = check_single(in_c, who)) return r;
+  dr_view* in = const_cast<dr_view*>(in_c);
+  if (op < DR_PLUS || op > DR_MAX) return fail(DR_E_INVAL, "%s: unknown op %d", who, op);
+  if (!init || !dev_result) return fail(DR_E_INVAL, "%s: NULL init or result", who);
+  if ((uintptr_t)dev_result % esize(in->dtype)) return fail(DR_E_ALIGN, "%s: result pointer misaligned", who);
+  cudaStream_t s = (cudaStream_t)stream;
+  static thread_local ReduceParams p;
+  std::memset(&p, 0, sizeof p);
+  p.vc = in->code();
+  p.op = op;
+  p.dtype = in->dtype;
+  p.result = dev_result;
+  std::memcpy(&p.init_bits, init, esize(in->dtype));
+  if (int r = call_pieces(in, nullptr, reduce_tile_elems(in->dtype), p.pc, &p.npieces, &p.ntiles)) return r;
+  const int grid = reduce_grid(in->dtype);
+  if (int r = in->ws_reduce.ensure(reduce_ws_bytes(grid), s)) return r;
+  p.ws = static_cast<char*>(in->ws_reduce.ptr);
+  p.status = status_word();
+  cudaError_t e = launch_reduce(p, grid, s);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
+}
+
+extern "C" int dr_scale_by_partner(const dr_vec* x, const dr_vec* y, const float* dev_g, dr_vec* gx,
+                                   dr_vec* gy, dr_stream_t stream) {
+  clear_error();
+  const char* who = "dr_scale_by_partner";
+  if (!x || !y || !dev_g) return fail(DR_E_INVAL, "%s: NULL argument", who);
+  if (!gx && !gy) return DR_OK;
+  if (x->dtype != DR_F32 || y->dtype != DR_F32 || (gx && gx->dtype != DR_F32) || (gy && gy->dtype != DR_F32))
+    return fail(DR_E_DTYPE, "%s: fp32 vectors only", who);
+  const int64_t n = x->n;
+  if (y->n != n || (gx && gx->n != n) || (gy && gy->n != n))
+    return fail(DR_E_INVAL, "%s: vectors must have equal length", who);
+  if (n == 0) return DR_OK;
+  std::vector<std::vector<Seg>> ops = {x->window(0, n), y->window(0, n)};
+  if (gx) ops.push_back(gx->window(0, n));
+  if (gy) ops.push_back(gy->window(0, n));
+  const std::vector<Piece> ps = resegment(ops, 4);
+  if ((int)ps.size() > kMaxPieces) return fail(DR_E_UNSUPPORTED, "%s: more than %d pieces", who, kMaxPieces);
+  static thread_local ScaleParams p;
+  std::memset(&p, 0, sizeof p);
+  p.g = dev_g;
+  p.npieces = (int)ps.size();
+  const int tile = scale_tile_elems();
+  int64_t t = 0;
+  for (size_t i = 0; i < ps.size(); ++i) {
+    auto& k = p.pc[i];
+    k.x = ps[i].p[0];
+    k.y = ps[i].p[1];
+    int o = 2;
+    k.gx = gx ? ps[i].p[o++] : nullptr;
+    k.gy = gy ? ps[i].p[o++] : nullptr;
+    k.len = ps[i].len;
+    k.tile_begin = t;
+    k.vec_ok = (uintptr_t)k.x % 16 == 0 && (uintptr_t)k.y % 16 == 0 && (uintptr_t)k.gx % 16 == 0 &&
+               (uintptr_t)k.gy % 16 == 0;
+    t += (k.len + tile - 1) / tile;
+  }
+  p.ntiles = t;
+  cudaError_t e = launch_scale(p, 0, (cudaStream_t)stream);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
+}
+
+static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
+                      cudaStream_t s) {
+  clear_error();
+  if (!in || !out) return fail(DR_E_INVAL, "%s: NULL array", who);
+  if (steps < 1) return fail(DR_E_INVAL, "%s: steps must be >= 1", who);
+  if (steps > 1 && !tmp) return fail(DR_E_INVAL, "%s: tmp is required when steps > 1", who);
+  auto same = [&](const dr_md2* m) {
+    return m->rows == in->rows && m->cols == in->cols && m->srows == in->srows;
+  };
+  if (!same(out) || (tmp && !same(tmp))) return fail(DR_E_INVAL, "%s: arrays differ in shape or blocking", who);
+  if (in == out || in == tmp || out == tmp) return fail(DR_E_INVAL, "%s: in, out, tmp must be distinct", who);
+  for (size_t k = 0; k < in->ptr.size(); ++k)
+    if (out->ptr[k] == in->ptr[k] || (tmp && (tmp->ptr[k] == in->ptr[k] || tmp->ptr[k] == out->ptr[k])))
+      return fail(DR_E_INVAL, "%s: in, out, tmp share storage", who);
+  const int nseg = (int)in->ptr.size();
+  int64_t nrb = 0;
+  for (int k = 0; k < nseg; ++k) nrb += (in->srows[k] + kStencilRowsPerCta - 1) / kStencilRowsPerCta;
+  if (nrb > 65535) return fail(DR_E_UNSUPPORTED, "%s: more than 65535 row blocks", who);
+  if (int r = exchange_halos(in, s)) return r;
+  static thread_local StencilParams p;
+  bool vec = in->cols % 4 == 0;
+  for (const dr_md2* m : {in, out, tmp})
+    if (m)
+      for (char* q : m->ptr) vec = vec && (uintptr_t)q % 16 == 0;
+  const dr_md2* src = in;
+  for (int t = 0; t < steps; ++t) {
+    dr_md2* dst = ((steps - 1 - t) % 2 == 0) ? out : tmp;
+    std::memset(&p, 0, sizeof p);
+    p.nseg = nseg;
+    p.cols = in->cols;
+    p.nrb = nrb;
+    p.wc = (float)wc;
+    p.wn = (float)wn;
+    p.vec_ok = vec ? 1 : 0;
+    int64_t rb = 0;
+    for (int k = 0; k < nseg; ++k) {
+      StencilSeg& g = p.seg[k];
+      g.in = reinterpret_cast<const float*>(src->ptr[k]);
+      g.out = reinterpret_cast<float*>(dst->ptr[k]);
+      g.out_prev = k > 0 ? reinterpret_cast<float*>(dst->ptr[k - 1]) : nullptr;
+      g.out_next = k + 1 < nseg ? reinterpret_cast<float*>(dst->ptr[k + 1]) : nullptr;
+      g.rows = in->srows[k];
+      g.prev_rows = k > 0 ? in->srows[k - 1] : 0;
+      g.rb_begin = rb;
+      rb += (in->srows[k] + kStencilRowsPerCta - 1) / kStencilRowsPerCta;
+    }
+    cudaError_t e = launch_stencil(p, s);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    src = dst;
+  }
+  return DR_OK;
+}
+
+extern "C" int dr_stencil5(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
+                           dr_stream_t stream) {
+  return do_stencil("dr_stencil5", in, out, tmp, steps, wc, wn, (cudaStream_t)stream);
+}
+
+// A^T of the zero-ghost-ring 5-point operator: column (k,l) of A^T is row (k,l)
+// of A, i.e. wc on the diagonal and wn on the in-grid neighbours, which is A.
+extern "C" int dr_stencil5_T(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
+                             dr_stream_t stream) {
+  return do_stencil("dr_stencil5_T", in, out, tmp, steps, wc, wn, (cudaStream_t)stream);
+}

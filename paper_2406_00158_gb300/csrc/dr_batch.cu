@@ -1,0 +1,406 @@
+// Host side of batched execution: the plan (device tables of pieces, tiles and
+// vectors), the one-launch run, its CUDA-graph replay, the one-launch-per-range
+// baseline, and the autotuner with its JSON cache.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "dr_batch.h"
+#include "dr_host.h"
+
+using namespace dr;
+
+struct dr_batch {
+  int nvec = 0;
+  int64_t total = 0;
+  std::vector<BPiece> pieces;
+  std::vector<int> vec_piece_begin;  // pieces of vector v: [begin[v], begin[v+1])
+  float* dots = nullptr;
+  dr_tune tune{256, 16, 4};
+  int sms = 1;
+  int device = -1;
+  int64_t ntiles = 0;
+  int64_t max_scan_tiles = 0;
+  BPiece* d_pieces = nullptr;
+  BTile* d_tiles = nullptr;
+  BVec* d_vecs = nullptr;
+  Workspace ws, ws_scan, ws_red;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap = nullptr;
+
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+  }
+  void free_tables() {
+    if (d_tiles) cudaFree(d_tiles);
+    if (d_vecs) cudaFree(d_vecs);
+    d_tiles = nullptr;
+    d_vecs = nullptr;
+  }
+};
+
+static int upload(void** dst, const void* src, size_t bytes) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  if (!bytes) bytes = 16;
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return fail(DR_E_NOMEM, "batch table allocation (%zu bytes): %s", bytes, cudaGetErrorString(e));
+  e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, "batch table upload");
+}
+
+// (Re)builds the tile table for the current launch shape and sizes the workspace.
+static int build_tiles(dr_batch* b) {
+  const int64_t TILE = (int64_t)b->tune.threads * b->tune.items;
+  std::vector<BTile> tiles;
+  std::vector<BVec> vecs(b->nvec);
+  for (int v = 0; v < b->nvec; ++v) {
+    vecs[v].first_tile = (int64_t)tiles.size();
+    for (int k = b->vec_piece_begin[v]; k < b->vec_piece_begin[v + 1]; ++k) {
+      const int64_t len = b->pieces[k].len;
+      if (len == 0) tiles.push_back(BTile{k, 0, 0});  // an empty vector still gets one tile
+      for (int64_t off = 0; off < len; off += TILE) tiles.push_back(BTile{k, 0, off});
+    }
+    vecs[v].ntiles = (int32_t)((int64_t)tiles.size() - vecs[v].first_tile);
+  }
+  b->free_tables();
+  if (int r = upload((void**)&b->d_tiles, tiles.data(), tiles.size() * sizeof(BTile))) return r;
+  if (int r = upload((void**)&b->d_vecs, vecs.data(), vecs.size() * sizeof(BVec))) return r;
+  b->ntiles = (int64_t)tiles.size();
+  if (int r = b->ws.ensure(batch_ws_bytes(b->ntiles, b->nvec), nullptr)) return r;
+  cudaError_t e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, "batch plan");
+}
+
+static bool tune_ok(const dr_tune* t) {
+  return t && batch_shape_supported(t->threads, t->items) && t->ctas_per_sm >= 1 && t->ctas_per_sm <= 8;
+}
+
+extern "C" int dr_batch_plan(int nvec, const dr_vec* const* x, const dr_vec* const* p, dr_vec* const* y,
+                             float* dev_dots, const dr_tune* tune, dr_batch** out) {
+  clear_error();
+  if (!out) return fail(DR_E_INVAL, "dr_batch_plan: out is NULL");
+  *out = nullptr;
+  if (nvec < 1 || !x || !p || !y || !dev_dots) return fail(DR_E_INVAL, "dr_batch_plan: NULL argument or nvec < 1");
+  if ((uintptr_t)dev_dots % 4) return fail(DR_E_ALIGN, "dr_batch_plan: dots pointer misaligned");
+  if (tune && !tune_ok(tune)) return fail(DR_E_INVAL, "dr_batch_plan: unsupported launch shape");
+  dr_batch* b = new (std::nothrow) dr_batch();
+  if (!b) return fail(DR_E_NOMEM, "dr_batch_plan: out of host memory");
+  b->nvec = nvec;
+  b->dots = dev_dots;
+  if (tune) b->tune = *tune;
+  b->sms = sm_count();
+  cudaGetDevice(&b->device);
+  b->vec_piece_begin.push_back(0);
+  for (int v = 0; v < nvec; ++v) {
+    if (!x[v] || !p[v] || !y[v]) {
+      delete b;
+      return fail(DR_E_INVAL, "dr_batch_plan: vector %d has a NULL operand", v);
+    }
+    if (x[v]->dtype != DR_F32 || p[v]->dtype != DR_F32 || y[v]->dtype != DR_F32) {
+      delete b;
+      return fail(DR_E_DTYPE, "dr_batch_plan: vector %d is not fp32", v);
+    }
+    const int64_t n = x[v]->n;
+    if (p[v]->n != n || y[v]->n != n) {
+      delete b;
+      return fail(DR_E_INVAL, "dr_batch_plan: vector %d operands differ in length", v);
+    }
+    const std::vector<Piece> ps = resegment({x[v]->window(0, n), p[v]->window(0, n), y[v]->window(0, n)}, 4);
+    if (ps.empty()) b->pieces.push_back(BPiece{nullptr, nullptr, nullptr, 0, v, 0});
+    int64_t scan_tiles = 0;
+    for (const Piece& q : ps) {
+      BPiece bp{reinterpret_cast<const float*>(q.p[0]), reinterpret_cast<const float*>(q.p[1]),
+                reinterpret_cast<float*>(q.p[2]), q.len, v, 0};
+      bp.vec_ok = (uintptr_t)bp.x % 16 == 0 && (uintptr_t)bp.p % 16 == 0 && (uintptr_t)bp.y % 16 == 0;
+      b->pieces.push_back(bp);
+      scan_tiles += (q.len + scan_tile_elems(DR_F32) - 1) / scan_tile_elems(DR_F32);
+    }
+    if (b->pieces.size() - b->vec_piece_begin.back() > (size_t)kMaxPieces) {
+      delete b;
+      return fail(DR_E_UNSUPPORTED, "dr_batch_plan: vector %d spans more than %d pieces", v, kMaxPieces);
+    }
+    b->max_scan_tiles = std::max(b->max_scan_tiles, scan_tiles);
+    b->vec_piece_begin.push_back((int)b->pieces.size());
+    b->total += n;
+  }
+  int r = upload((void**)&b->d_pieces, b->pieces.data(), b->pieces.size() * sizeof(BPiece));
+  if (!r) r = build_tiles(b);
+  if (r) {
+    dr_batch_destroy(b);
+    return r;
+  }
+  *out = b;
+  return DR_OK;
+}
+
+extern "C" int dr_batch_destroy(dr_batch* b) {
+  clear_error();
+  if (!b) return DR_OK;
+  b->drop_graph();
+  if (b->cap) cudaStreamDestroy(b->cap);
+  b->free_tables();
+  if (b->d_pieces) cudaFree(b->d_pieces);
+  b->ws.release();
+  b->ws_scan.release();
+  b->ws_red.release();
+  delete b;
+  return DR_OK;
+}
+
+extern "C" int dr_batch_set_tune(dr_batch* b, const dr_tune* tune) {
+  clear_error();
+  if (!b) return fail(DR_E_INVAL, "dr_batch_set_tune: NULL plan");
+  if (!tune_ok(tune)) return fail(DR_E_INVAL, "dr_batch_set_tune: unsupported launch shape");
+  const bool retile = tune->threads * tune->items != b->tune.threads * b->tune.items;
+  b->tune = *tune;
+  b->drop_graph();
+  return retile ? build_tiles(b) : DR_OK;
+}
+
+extern "C" int dr_batch_get_tune(const dr_batch* b, dr_tune* tune) {
+  clear_error();
+  if (!b || !tune) return fail(DR_E_INVAL, "dr_batch_get_tune: NULL argument");
+  *tune = b->tune;
+  return DR_OK;
+}
+
+static BatchParams params_of(const dr_batch* b) {
+  BatchParams p{};
+  p.pieces = b->d_pieces;
+  p.tiles = b->d_tiles;
+  p.vecs = b->d_vecs;
+  p.ntiles = b->ntiles;
+  p.nvec = b->nvec;
+  p.ws = static_cast<char*>(b->ws.ptr);
+  p.dots = b->dots;
+  p.status = status_word();
+  p.spin_limit = spin_limit();
+  return p;
+}
+
+extern "C" int dr_batch_run(dr_batch* b, dr_stream_t stream) {
+  clear_error();
+  if (!b) return fail(DR_E_INVAL, "dr_batch_run: NULL plan");
+  const BatchParams p = params_of(b);
+  if (!p.status) return fail(DR_E_CUDA, "dr_batch_run: no device status word");
+  cudaError_t e = launch_batch(p, b->tune, b->sms, (cudaStream_t)stream);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, "dr_batch_run");
+}
+
+extern "C" int dr_batch_run_graph(dr_batch* b, dr_stream_t stream) {
+  clear_error();
+  if (!b) return fail(DR_E_INVAL, "dr_batch_run_graph: NULL plan");
+  cudaError_t e;
+  if (!b->gexec) {
+    if (!b->cap && (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "capture stream");
+    const BatchParams p = params_of(b);
+    if (!p.status) return fail(DR_E_CUDA, "dr_batch_run_graph: no device status word");
+    if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    cudaError_t le = launch_batch(p, b->tune, b->sms, b->cap);
+    e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (le != cudaSuccess) return cuda_fail(le, "launch under capture");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if ((e = cudaGraphInstantiate(&b->gexec, b->graph, 0)) != cudaSuccess) {
+      b->drop_graph();
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  e = cudaGraphLaunch(b->gexec, (cudaStream_t)stream);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+// One single-range scan launch and one single-range dot launch per vector.
+extern "C" int dr_batch_run_per_range(dr_batch* b, dr_stream_t stream) {
+  clear_error();
+  if (!b) return fail(DR_E_INVAL, "dr_batch_run_per_range: NULL plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rgrid = reduce_grid(DR_F32);
+  if (int r = b->ws_scan.ensure(scan_ws_bytes(std::max<int64_t>(1, b->max_scan_tiles), DR_F32), s)) return r;
+  if (int r = b->ws_red.ensure(reduce_ws_bytes(rgrid), s)) return r;
+  unsigned* status = status_word();
+  if (!status) return fail(DR_E_CUDA, "dr_batch_run_per_range: no device status word");
+  static thread_local ScanParams sp;
+  static thread_local ReduceParams rp;
+  const int st = scan_tile_elems(DR_F32), rt = reduce_tile_elems(DR_F32);
+  for (int v = 0; v < b->nvec; ++v) {
+    const int k0 = b->vec_piece_begin[v], k1 = b->vec_piece_begin[v + 1];
+    std::memset(&sp, 0, sizeof sp);
+    std::memset(&rp, 0, sizeof rp);
+    int64_t ts = 0, tr = 0;
+    int np = 0;
+    for (int k = k0; k < k1; ++k) {
+      const BPiece& q = b->pieces[k];
+      if (q.len == 0) continue;
+      KPiece& a = sp.pc[np];
+      a.a = reinterpret_cast<const char*>(q.x);
+      a.o = reinterpret_cast<char*>(q.y);
+      a.len = q.len;
+      a.tile_begin = ts;
+      a.vec_ok = (uintptr_t)q.x % 16 == 0 && (uintptr_t)q.y % 16 == 0;
+      ts += (q.len + st - 1) / st;
+      KPiece& c = rp.pc[np];
+      c.a = reinterpret_cast<const char*>(q.x);
+      c.b = reinterpret_cast<const char*>(q.p);
+      c.len = q.len;
+      c.tile_begin = tr;
+      c.vec_ok = (uintptr_t)q.x % 16 == 0 && (uintptr_t)q.p % 16 == 0;
+      tr += (q.len + rt - 1) / rt;
+      ++np;
+    }
+    sp.vc.kind = 0;
+    sp.vc.nleaf = 1;
+    sp.op = DR_PLUS;
+    sp.dtype = DR_F32;
+    sp.npieces = np;
+    sp.ntiles = ts;
+    sp.ws = static_cast<char*>(b->ws_scan.ptr);
+    sp.status = status;
+    sp.spin_limit = spin_limit();
+    sp.skip_tile = -1;
+    rp.vc.kind = 1;
+    rp.vc.nleaf = 2;
+    rp.vc.zipop = DR_MUL;
+    rp.op = DR_PLUS;
+    rp.dtype = DR_F32;
+    rp.npieces = np;
+    rp.ntiles = tr;
+    rp.ws = static_cast<char*>(b->ws_red.ptr);
+    rp.status = status;
+    rp.result = b->dots + v;
+    if (np > 0) {
+      cudaError_t e = launch_scan(sp, false, 0, s);
+      if (e != cudaSuccess) return cuda_fail(e, "per-range scan launch");
+    }
+    cudaError_t e = launch_reduce(rp, rgrid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "per-range dot launch");
+  }
+  return DR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+static std::string tune_key(const dr_batch* b) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, b->device < 0 ? 0 : b->device);
+  char buf[512];
+  const int lt = b->total > 0 ? (int)std::floor(std::log2((double)b->total)) : 0;
+  const int lv = (int)std::floor(std::log2((double)b->nvec));
+  std::snprintf(buf, sizeof buf, "%s|sms=%d|batch_scan_dot_f32|log2n=%d|log2nvec=%d", prop.name, b->sms, lt, lv);
+  return buf;
+}
+
+static bool cache_lookup(const char* path, const std::string& key, dr_tune* t) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::string line, pat = "\"" + key + "\":";
+  while (std::getline(f, line)) {
+    const size_t k = line.find(pat);
+    if (k == std::string::npos) continue;
+    dr_tune c{};
+    const char* s = line.c_str() + k + pat.size();
+    if (std::sscanf(s, " {\"threads\": %d, \"items\": %d, \"ctas_per_sm\": %d", &c.threads, &c.items,
+                    &c.ctas_per_sm) == 3 &&
+        tune_ok(&c)) {
+      *t = c;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void cache_store(const char* path, const std::string& key, const dr_tune& t, double us) {
+  std::vector<std::string> keep;
+  {
+    std::ifstream f(path);
+    std::string line, pat = "\"" + key + "\":";
+    while (f && std::getline(f, line))
+      if (line.find("\":") != std::string::npos && line.find(pat) == std::string::npos) {
+        while (!line.empty() && (line.back() == ',' || line.back() == ' ')) line.pop_back();
+        keep.push_back(line);
+      }
+  }
+  char buf[640];
+  std::snprintf(buf, sizeof buf, "\"%s\": {\"threads\": %d, \"items\": %d, \"ctas_per_sm\": %d, \"us\": %.2f}",
+                key.c_str(), t.threads, t.items, t.ctas_per_sm, us);
+  keep.push_back(buf);
+  const std::string tmp = std::string(path) + ".tmp";
+  {
+    std::ofstream o(tmp);
+    o << "{\n";
+    for (size_t i = 0; i < keep.size(); ++i) o << keep[i] << (i + 1 < keep.size() ? ",\n" : "\n");
+    o << "}\n";
+  }
+  std::rename(tmp.c_str(), path);
+}
+
+extern "C" int dr_batch_autotune(dr_batch* b, int mode, const char* cache_path, dr_tune* chosen) {
+  clear_error();
+  if (!b) return fail(DR_E_INVAL, "dr_batch_autotune: NULL plan");
+  if (!cache_path) cache_path = std::getenv("DR_TUNE_CACHE");
+  const std::string key = tune_key(b);
+  dr_tune best{};
+  if (mode == 0 && cache_path && cache_lookup(cache_path, key, &best)) {
+    if (int r = dr_batch_set_tune(b, &best)) return r;
+    if (chosen) *chosen = best;
+    return DR_OK;
+  }
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune stream");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best_us = 1e30;
+  const int shapes[][2] = {{128, 16}, {256, 8}, {256, 16}, {512, 8}, {512, 16}};
+  const int ctas[] = {1, 2, 4, 8};
+  int rc = DR_OK;
+  for (const auto& sh : shapes) {
+    for (int k : ctas) {
+      dr_tune t{sh[0], sh[1], k};
+      if ((rc = dr_batch_set_tune(b, &t))) break;
+      for (int w = 0; w < 2; ++w) dr_batch_run(b, (dr_stream_t)s);
+      std::vector<float> ms;
+      for (int it = 0; it < 5; ++it) {
+        cudaEventRecord(e0, s);
+        dr_batch_run(b, (dr_stream_t)s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float m = 0.f;
+        cudaEventElapsedTime(&m, e0, e1);
+        ms.push_back(m);
+      }
+      std::sort(ms.begin(), ms.end());
+      const double us = ms[ms.size() / 2] * 1e3;
+      if (us < best_us) {
+        best_us = us;
+        best = t;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (rc) return rc;
+  if (int r = dr_sync_status(nullptr)) return r;
+  if (int r = dr_batch_set_tune(b, &best)) return r;
+  if (cache_path && *cache_path) cache_store(cache_path, key, best, best_us);
+  if (chosen) *chosen = best;
+  return DR_OK;
+}

@@ -1,0 +1,339 @@
+// Device-side helpers shared by the kernels of the segmented-range library:
+// element types and operators, 128-bit access, memory-model-explicit flag
+// loads/stores (PTX), bounded waits and warp-level scan / reduce building blocks.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dr_kernels.h"
+
+namespace dr {
+
+// --------------------------------------------------------------------------
+// operators
+// --------------------------------------------------------------------------
+template <typename T>
+struct Lim;
+template <>
+struct Lim<float> {
+  static __device__ __forceinline__ float lowest() { return -__int_as_float(0x7f800000); }
+  static __device__ __forceinline__ float highest() { return __int_as_float(0x7f800000); }
+};
+template <>
+struct Lim<double> {
+  static __device__ __forceinline__ double lowest() { return -__longlong_as_double(0x7ff0000000000000ll); }
+  static __device__ __forceinline__ double highest() { return __longlong_as_double(0x7ff0000000000000ll); }
+};
+template <>
+struct Lim<long long> {
+  static __device__ __forceinline__ long long lowest() { return (long long)0x8000000000000000ull; }
+  static __device__ __forceinline__ long long highest() { return 0x7fffffffffffffffll; }
+};
+template <>
+struct Lim<int> {
+  static __device__ __forceinline__ int lowest() { return (int)0x80000000u; }
+  static __device__ __forceinline__ int highest() { return 0x7fffffff; }
+};
+
+// Integer adds and multiplies wrap (done in the unsigned type).
+template <typename T>
+__device__ __forceinline__ T wrap_add(T a, T b) { return a + b; }
+template <>
+__device__ __forceinline__ long long wrap_add(long long a, long long b) {
+  return (long long)((unsigned long long)a + (unsigned long long)b);
+}
+template <>
+__device__ __forceinline__ int wrap_add(int a, int b) { return (int)((unsigned)a + (unsigned)b); }
+template <typename T>
+__device__ __forceinline__ T wrap_mul(T a, T b) { return a * b; }
+template <>
+__device__ __forceinline__ long long wrap_mul(long long a, long long b) {
+  return (long long)((unsigned long long)a * (unsigned long long)b);
+}
+template <>
+__device__ __forceinline__ int wrap_mul(int a, int b) { return (int)((unsigned)a * (unsigned)b); }
+
+template <int OP>
+struct Op {
+  template <typename T>
+  static __device__ __forceinline__ T apply(T a, T b) {
+    if constexpr (OP == DR_PLUS) return wrap_add(a, b);
+    else if constexpr (OP == DR_MUL) return wrap_mul(a, b);
+    else if constexpr (OP == DR_MIN) return b < a ? b : a;
+    else return a < b ? b : a;
+  }
+  template <typename T>
+  static __device__ __forceinline__ T identity() {
+    if constexpr (OP == DR_PLUS) return T(0);
+    else if constexpr (OP == DR_MUL) return T(1);
+    else if constexpr (OP == DR_MIN) return Lim<T>::highest();
+    else return Lim<T>::lowest();
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T binop_rt(int op, T a, T b) {
+  switch (op) {
+    case DR_PLUS: return wrap_add(a, b);
+    case DR_MUL: return wrap_mul(a, b);
+    case DR_MIN: return b < a ? b : a;
+    default: return a < b ? b : a;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T unop_rt(int op, T x, T a) {
+  switch (op) {
+    case DR_U_SCALE: return wrap_mul(a, x);
+    case DR_U_ADD: return wrap_add(x, a);
+    case DR_U_NEG: return wrap_mul(T(-1), x);
+    case DR_U_ABS: return x < T(0) ? wrap_mul(T(-1), x) : x;
+    default: return wrap_mul(x, x);
+  }
+}
+
+// The fused view of a kernel: nleaf operands, each with a chain of unary ops,
+// combined by zipop (if two), then a chain of unary ops.
+template <typename T>
+struct ViewEval {
+  int nleaf, zipop, npre[2], npost;
+  int pre_op[2][kMaxChain], post_op[kMaxChain];
+  T pre_arg[2][kMaxChain], post_arg[kMaxChain];
+
+  __device__ __forceinline__ void init(const KViewCode& c) {
+    nleaf = c.nleaf;
+    zipop = c.zipop;
+    npost = c.npost;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      npre[l] = c.npre[l];
+#pragma unroll
+      for (int k = 0; k < kMaxChain; ++k) {
+        pre_op[l][k] = c.pre_op[l][k];
+        pre_arg[l][k] = (T)c.pre_arg[l][k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxChain; ++k) {
+      post_op[k] = c.post_op[k];
+      post_arg[k] = (T)c.post_arg[k];
+    }
+  }
+  __device__ __forceinline__ T operator()(T a, T b) const {
+#pragma unroll
+    for (int k = 0; k < kMaxChain; ++k)
+      if (k < npre[0]) a = unop_rt(pre_op[0][k], a, pre_arg[0][k]);
+    if (nleaf == 2) {
+#pragma unroll
+      for (int k = 0; k < kMaxChain; ++k)
+        if (k < npre[1]) b = unop_rt(pre_op[1][k], b, pre_arg[1][k]);
+      a = binop_rt(zipop, a, b);
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxChain; ++k)
+      if (k < npost) a = unop_rt(post_op[k], a, post_arg[k]);
+    return a;
+  }
+};
+
+// --------------------------------------------------------------------------
+// 128-bit access
+// --------------------------------------------------------------------------
+template <typename T>
+struct V16 {
+  static constexpr int N = 16 / sizeof(T);
+  T v[N];
+};
+
+template <typename T>
+__device__ __forceinline__ V16<T> ld16(const void* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  V16<T> o;
+  memcpy(&o, &r, 16);
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void st16(void* p, const V16<T>& o) {
+  uint4 r;
+  memcpy(&r, &o, 16);
+  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(r.x), "r"(r.y), "r"(r.z),
+               "r"(r.w)
+               : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T ld1(const void* p) {
+  return __ldg(reinterpret_cast<const T*>(p));
+}
+
+// --------------------------------------------------------------------------
+// memory-model-explicit accesses (gpu scope)
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned long long to_bits(T v) {
+  if constexpr (sizeof(T) == 4) {
+    unsigned u;
+    memcpy(&u, &v, 4);
+    return u;
+  } else {
+    unsigned long long u;
+    memcpy(&u, &v, 8);
+    return u;
+  }
+}
+template <typename T>
+__device__ __forceinline__ T from_bits(unsigned long long u) {
+  T v;
+  if constexpr (sizeof(T) == 4) {
+    unsigned w = (unsigned)u;
+    memcpy(&v, &w, 4);
+  } else {
+    memcpy(&v, &u, 8);
+  }
+  return v;
+}
+
+// --------------------------------------------------------------------------
+// Lookback slots.  Tile i publishes (state, value): state A = the tile's own
+// aggregate, state P = the inclusive prefix through the tile.  A flag is
+// (epoch << 2) | state and is valid only for the current launch's epoch, so the
+// slots never need clearing between launches.
+//   4-byte T: flag and value packed in one 64-bit word (single-copy atomic).
+//   8-byte T: a 32-bit flag published with release after the value; readers
+//             load the flag with acquire, then the value.
+// --------------------------------------------------------------------------
+constexpr unsigned kStateA = 1, kStateP = 2;
+
+template <typename T, bool PACKED = (sizeof(T) == 4)>
+struct Slots;
+
+template <typename T>
+struct Slots<T, true> {
+  unsigned long long* w;
+  static __host__ __device__ size_t bytes(int64_t ntiles) { return (size_t)ntiles * 8; }
+  __device__ void bind(char* base, int64_t) { w = reinterpret_cast<unsigned long long*>(base); }
+  __device__ __forceinline__ void publish(int64_t i, unsigned tag, unsigned state, T v) {
+    st_relaxed_u64(w + i, ((unsigned long long)(tag | state) << 32) | to_bits(v));
+  }
+  // returns the state (0 if not yet valid for this epoch)
+  __device__ __forceinline__ unsigned poll(int64_t i, unsigned tag, T& v) const {
+    unsigned long long x = ld_relaxed_u64(w + i);
+    unsigned f = (unsigned)(x >> 32);
+    if ((f & ~3u) != tag) return 0;
+    v = from_bits<T>(x & 0xffffffffull);
+    return f & 3u;
+  }
+};
+
+template <typename T>
+struct Slots<T, false> {
+  unsigned* flag;
+  T* agg;
+  T* pfx;
+  static __host__ __device__ size_t bytes(int64_t ntiles) {
+    return ((size_t)ntiles * 4 + 15) / 16 * 16 + (size_t)ntiles * 16;
+  }
+  __device__ void bind(char* base, int64_t ntiles) {
+    flag = reinterpret_cast<unsigned*>(base);
+    agg = reinterpret_cast<T*>(base + ((size_t)ntiles * 4 + 15) / 16 * 16);
+    pfx = agg + ntiles;
+  }
+  __device__ __forceinline__ void publish(int64_t i, unsigned tag, unsigned state, T v) {
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(state == kStateP ? pfx + i : agg + i);
+    st_relaxed_u64(dst, to_bits(v));
+    st_release_u32(flag + i, tag | state);
+  }
+  __device__ __forceinline__ unsigned poll(int64_t i, unsigned tag, T& v) const {
+    unsigned f = ld_acquire_u32(flag + i);
+    if ((f & ~3u) != tag) return 0;
+    unsigned s = f & 3u;
+    const unsigned long long* src =
+        reinterpret_cast<const unsigned long long*>(s == kStateP ? pfx + i : agg + i);
+    v = from_bits<T>(ld_relaxed_u64(src));
+    return s;
+  }
+};
+
+// Records a device-side failure in the status word (first writer wins).
+__device__ __forceinline__ void raise_status(unsigned* status, unsigned code, unsigned info) {
+  if (atomicCAS(status, 0u, code) == 0u) atomicExch(status + 1, info);
+}
+
+// Polls slot i until it is valid for this epoch.  Bounded: gives up after
+// `limit` polls (or as soon as another wait on the device has given up),
+// records DR_E_TIMEOUT and returns P with the identity so the caller finishes.
+template <typename T, typename S, typename OPT>
+__device__ __forceinline__ unsigned wait_slot(const S& slots, int64_t i, unsigned tag, T& v,
+                                              int64_t limit, unsigned* status) {
+  unsigned s = slots.poll(i, tag, v);
+  if (s) return s;
+  unsigned ns = 32;
+  for (int64_t polls = 1;; ++polls) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    s = slots.poll(i, tag, v);
+    if (s) return s;
+    if (polls >= limit) {
+      raise_status(status, DR_E_TIMEOUT, (unsigned)i);
+      break;
+    }
+    if ((polls & 31) == 0 && ld_relaxed_u32(status) != 0u) break;
+  }
+  v = OPT::template identity<T>();
+  return kStateP;
+}
+
+// --------------------------------------------------------------------------
+// warp building blocks
+// --------------------------------------------------------------------------
+template <typename T, int OP>
+__device__ __forceinline__ T warp_reduce(T v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v = Op<OP>::apply(v, __shfl_xor_sync(0xffffffffu, v, d));
+  return v;
+}
+
+// Inclusive scan across the lanes of a warp; REV = from lane 31 down to lane 0.
+template <typename T, int OP, bool REV>
+__device__ __forceinline__ T warp_inclusive(T v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    if constexpr (!REV) {
+      T y = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d) v = Op<OP>::apply(y, v);
+    } else {
+      T y = __shfl_down_sync(0xffffffffu, v, d);
+      if (lane + d < 32) v = Op<OP>::apply(y, v);
+    }
+  }
+  return v;
+}
+
+}  // namespace dr

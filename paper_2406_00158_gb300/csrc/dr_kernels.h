@@ -1,0 +1,151 @@
+// Interface between the host side of the library (dr_api.cu: handles, views,
+// re-segmentation, validation) and the kernel translation units.  Kernel
+// parameters are plain structs passed by value (__grid_constant__), so a call
+// over up to kMaxPieces segments needs no device-side table.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dr.h"
+
+namespace dr {
+
+constexpr int kMaxChain = 4;     // unary ops per chain in a fused view
+constexpr int kMaxPieces = 128;  // segments (after re-segmentation) per single-range call
+
+// Fused view: element = post(zipop(pre0(a), pre1(b))) (or post(pre0(a)) for one leaf).
+// kind: 0 = one leaf, no ops; 1 = two leaves times each other, no other ops
+// (the dot product); 2 = anything else (interpreted per element, uniform branches).
+struct KViewCode {
+  int kind;
+  int nleaf;
+  int zipop;
+  int npre[2];
+  int npost;
+  int pre_op[2][kMaxChain];
+  int post_op[kMaxChain];
+  double pre_arg[2][kMaxChain];
+  double post_arg[kMaxChain];
+};
+
+// One piece of a call: `len` elements, operands at a / b, output at o (byte
+// pointers at the piece's first element), first tile index of the piece in the
+// call's global tile order.  vec_ok: all of a, b, o are 16-byte aligned.
+struct KPiece {
+  const char* a;
+  const char* b;
+  char* o;
+  int64_t len;
+  int64_t tile_begin;
+  int32_t vec_ok;
+  int32_t pad_;
+};
+
+// Self-cleaning workspace header: the last CTA of every launch restores
+// ticket = done = 0 and advances epoch, so no memset is needed between launches.
+struct WsHeader {
+  unsigned long long ticket;
+  unsigned done;
+  unsigned epoch;
+  unsigned long long pad_[6];
+};
+static_assert(sizeof(WsHeader) == 64, "header size");
+
+struct ReduceParams {
+  KViewCode vc;
+  int op;
+  int dtype;
+  int npieces;
+  int64_t ntiles;
+  char* ws;          // WsHeader + one partial (8 bytes) per CTA
+  unsigned* status;  // per-device status word
+  void* result;      // one element of dtype
+  unsigned long long init_bits;
+  KPiece pc[kMaxPieces];
+};
+
+struct ScanParams {
+  KViewCode vc;
+  int op;
+  int dtype;
+  int npieces;
+  int exclusive;
+  int64_t ntiles;
+  char* ws;  // WsHeader + lookback slots
+  unsigned* status;
+  int64_t spin_limit;
+  int64_t skip_tile;  // test hook: this logical tile never publishes (-1: none)
+  unsigned long long init_bits;
+  KPiece pc[kMaxPieces];
+};
+
+struct ScaleParams {  // dot adjoint: gx = g*y, gy = g*x
+  const float* g;
+  int npieces;
+  int64_t ntiles;
+  struct P4 {
+    const char* x;
+    const char* y;
+    char* gx;
+    char* gy;
+    int64_t len;
+    int64_t tile_begin;
+    int32_t vec_ok;
+    int32_t pad_;
+  } pc[kMaxPieces];
+};
+
+struct StencilSeg {
+  const float* in;   // allocation incl. ghost rows: (rows + 2) * cols
+  float* out;
+  float* out_prev;   // output allocation of the block above (NULL for the first)
+  float* out_next;   // output allocation of the block below (NULL for the last)
+  int64_t rows;
+  int64_t prev_rows; // own rows of the block above
+  int64_t rb_begin;  // first row-block index of this segment
+};
+
+struct StencilParams {
+  int nseg;
+  int64_t cols;
+  int64_t nrb;       // total row blocks
+  float wc, wn;
+  int vec_ok;        // cols % 4 == 0 and all pointers 16-byte aligned
+  StencilSeg seg[kMaxPieces];
+};
+
+struct HaloParams {
+  int nbound;  // interior boundaries
+  int64_t cols;
+  struct B {
+    const float* src_last;  // block k's last own row
+    float* dst_top_ghost;   // block k+1's row 0
+    const float* src_first; // block k+1's first own row
+    float* dst_bot_ghost;   // block k's bottom ghost row
+  } b[kMaxPieces];
+};
+
+// Tile geometry (elements per tile) of each kernel family for a dtype.
+int reduce_tile_elems(int dtype);
+int scan_tile_elems(int dtype);
+int scale_tile_elems();
+constexpr int kStencilThreads = 128;   // 4 columns per thread -> 512 columns per CTA
+constexpr int kStencilRowsPerCta = 64;
+
+size_t reduce_ws_bytes(int grid);
+size_t scan_ws_bytes(int64_t ntiles, int dtype);
+
+// Launchers (kernel TUs).  Return the launch's cudaError_t.
+cudaError_t launch_reduce(const ReduceParams& p, int grid, cudaStream_t s);
+cudaError_t launch_scan(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
+cudaError_t launch_scale(const ScaleParams& p, int grid, cudaStream_t s);
+cudaError_t launch_stencil(const StencilParams& p, cudaStream_t s);
+cudaError_t launch_halo(const HaloParams& p, cudaStream_t s);
+
+// Resident-CTA count helpers (host).
+int reduce_grid(int dtype);
+int scan_grid(int dtype, int64_t ntiles);
+
+}  // namespace dr

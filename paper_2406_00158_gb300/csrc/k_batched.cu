@@ -1,0 +1,263 @@
+// Batched execution: for many independent segmented fp32 vectors, y_v =
+// inclusive_scan(x_v) and dots[v] = <x_v, p_v>, all in ONE persistent launch.
+//
+// The single-range kernels need one launch per vector per algorithm; with
+// thousands of short vectors that is launch-bound (cf. the launch fan-out cost
+// of a single-process runtime, Sec. 5 "Reduce").  Here every vector is cut into
+// tiles (per segment, as in the single-range kernels) and all tiles form one
+// global order, vector after vector.  Persistent CTAs take tiles from an
+// atomic ticket; each tile reads x and p once (128-bit), writes y once:
+// 12 B / element for both algorithms together.
+//  * scan carry: decoupled lookback over the tile's predecessors *within its
+//    vector* (the vector's first tile publishes its inclusive prefix directly);
+//  * dot: each tile writes its partial; the vector's last tile to finish
+//    (per-vector counter) combines the partials in tile order: deterministic.
+// Launch shape (threads per CTA, elements per thread, CTAs per SM) is a
+// template / launch parameter chosen by the autotuner.
+#include "dr_batch.h"
+#include "dr_device.cuh"
+
+namespace dr {
+namespace {
+
+__device__ __forceinline__ float fadd(float a, float b) { return a + b; }
+
+template <int THREADS, int CH>
+__global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ BatchParams P) {
+  constexpr int NW = THREADS / 32;
+  constexpr int Q = CH * NW;             // warp-chunk totals per tile
+  constexpr int R = (Q + 31) / 32;       // entries per lane in warp 0
+  constexpr int TILE = THREADS * CH * 4;
+  using O = Op<DR_PLUS>;
+  __shared__ float s_tot[R * 32];
+  __shared__ float s_off[R * 32];
+  __shared__ float s_dot[NW];
+  __shared__ long long s_ticket;
+  __shared__ int s_last;
+
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
+  // layout: header | per-vector counters | lookback slots | per-tile dot partials
+  // (counters first: their offset does not depend on the tile count)
+  unsigned* vcount = reinterpret_cast<unsigned*>(P.ws + sizeof(WsHeader));
+  char* slot_base = P.ws + sizeof(WsHeader) + ((size_t)P.nvec * 4 + 15) / 16 * 16;
+  Slots<float> slots;
+  slots.bind(slot_base, P.ntiles);
+  float* dotpart = reinterpret_cast<float*>(slot_base + Slots<float>::bytes(P.ntiles));
+  const unsigned tag = (ld_relaxed_u32(&hdr->epoch) & 0x3fffffffu) << 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  while (true) {
+    if (tid == 0) s_ticket = (long long)atomicAdd(&hdr->ticket, 1ull);
+    __syncthreads();
+    const int64_t t = s_ticket;
+    if (t >= P.ntiles) break;
+    const BTile bt = P.tiles[t];
+    const BPiece pc = P.pieces[bt.piece];
+    const BVec bv = P.vecs[pc.vec];
+    const int64_t base = bt.off;
+    const bool full = pc.vec_ok && pc.len - base >= TILE;
+
+    float x[CH][4], pr[CH][4];
+    if (full) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        V16<float> a = ld16<float>(pc.x + base + (int64_t)(c * THREADS + tid) * 4);
+        V16<float> b = ld16<float>(pc.p + base + (int64_t)(c * THREADS + tid) * 4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          x[c][e] = a.v[e];
+          pr[c][e] = b.v[e];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int64_t i = base + (int64_t)(c * THREADS + tid) * 4 + e;
+          const bool in = i < pc.len;
+          x[c][e] = in ? __ldg(pc.x + i) : 0.f;
+          pr[c][e] = in ? __ldg(pc.p + i) : 0.f;
+        }
+    }
+
+    // dot partial of the tile (fixed order)
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      d0 = __fmaf_rn(x[c][0], pr[c][0], d0);
+      d1 = __fmaf_rn(x[c][1], pr[c][1], d1);
+      d2 = __fmaf_rn(x[c][2], pr[c][2], d2);
+      d3 = __fmaf_rn(x[c][3], pr[c][3], d3);
+    }
+    float dsum = warp_reduce<float, DR_PLUS>((d0 + d1) + (d2 + d3));
+    if (lane == 0) s_dot[warp] = dsum;
+
+    // thread-local and warp scans of x
+    float tsum[CH], wexc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      x[c][1] = fadd(x[c][0], x[c][1]);
+      x[c][2] = fadd(x[c][1], x[c][2]);
+      x[c][3] = fadd(x[c][2], x[c][3]);
+      tsum[c] = x[c][3];
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const float wi = warp_inclusive<float, DR_PLUS, false>(tsum[c], lane);
+      float we = __shfl_up_sync(0xffffffffu, wi, 1);
+      if (lane == 0) we = 0.f;
+      wexc[c] = we;
+      const float wt = __shfl_sync(0xffffffffu, wi, 31);
+      if (lane == 0) s_tot[c * NW + warp] = wt;
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+      // the tile's dot partial
+      if (lane == 0) {
+        float dt = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) dt += s_dot[w];
+        dotpart[t] = dt;
+      }
+      // block-level scan of the Q warp-chunk totals: R consecutive entries per lane
+      float loc[R];
+      float lsum = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int q = lane * R + r;
+        loc[r] = q < Q ? s_tot[q] : 0.f;
+        lsum = r == 0 ? loc[0] : fadd(lsum, loc[r]);
+      }
+      const float inc = warp_inclusive<float, DR_PLUS, false>(lsum, lane);
+      const float agg = __shfl_sync(0xffffffffu, inc, 31);
+      float exc = __shfl_up_sync(0xffffffffu, inc, 1);
+      if (lane == 0) exc = 0.f;
+
+      float prefix = 0.f;
+      const int64_t first = bv.first_tile;
+      if (t == first) {
+        if (lane == 0) slots.publish(t, tag, kStateP, agg);
+      } else {
+        if (lane == 0) slots.publish(t, tag, kStateA, agg);
+        int64_t pred = t - 1;
+        float run = 0.f;
+        while (true) {
+          const int64_t i = pred - lane;
+          float val = 0.f;
+          unsigned st = kStateP;  // before the vector's first tile: identity
+          if (i >= first) st = slots.poll(i, tag, val);
+          unsigned pm = __ballot_sync(0xffffffffu, st == kStateP);
+          const int lim = pm ? __ffs(pm) - 1 : 32;
+          if (st == 0 && lane < lim)
+            st = wait_slot<float, Slots<float>, O>(slots, i, tag, val, P.spin_limit, P.status);
+          __syncwarp();
+          pm = __ballot_sync(0xffffffffu, st == kStateP);
+          const int fl = pm ? __ffs(pm) - 1 : 31;
+          const float w = warp_reduce<float, DR_PLUS>(lane <= fl ? val : 0.f);
+          run = w + run;
+          if (pm) break;
+          pred -= 32;
+        }
+        prefix = run;
+        if (lane == 0) slots.publish(t, tag, kStateP, prefix + agg);
+      }
+      float o = fadd(prefix, exc);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int q = lane * R + r;
+        if (q < Q) s_off[q] = o;
+        o = fadd(o, loc[r]);
+      }
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const float pre = fadd(s_off[c * NW + warp], wexc[c]);
+      float y[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) y[e] = fadd(pre, x[c][e]);
+      const int64_t off = base + (int64_t)(c * THREADS + tid) * 4;
+      if (full) {
+        V16<float> q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) q.v[e] = y[e];
+        st16<float>(pc.y + off, q);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (off + e < pc.len) pc.y[off + e] = y[e];
+      }
+    }
+
+    // the vector's last tile to finish combines the dot partials in tile order
+    if (tid == 0) {
+      __threadfence();
+      s_last = atomicAdd(vcount + pc.vec, 1u) == (unsigned)bv.ntiles - 1;
+    }
+    __syncthreads();
+    if (s_last && warp == 0) {
+      __threadfence();
+      float acc = 0.f;
+      for (int64_t i = bv.first_tile + lane; i < bv.first_tile + bv.ntiles; i += 32)
+        acc += __int_as_float((int)ld_relaxed_u32(reinterpret_cast<const unsigned*>(dotpart + i)));
+      acc = warp_reduce<float, DR_PLUS>(acc);
+      if (lane == 0) {
+        P.dots[pc.vec] = acc;
+        vcount[pc.vec] = 0;
+      }
+    }
+    __syncthreads();
+  }
+
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&hdr->done, 1u) == gridDim.x - 1) {
+      hdr->ticket = 0;
+      hdr->done = 0;
+      hdr->epoch = hdr->epoch + 1;
+      __threadfence();
+    }
+  }
+}
+
+template <int THREADS, int CH>
+cudaError_t go(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s) {
+  static int per = 0;
+  if (!per) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<THREADS, CH>, THREADS, 0);
+    if (per < 1) per = 1;
+  }
+  const int k = ctas_per_sm < per ? ctas_per_sm : per;
+  int64_t grid = (int64_t)sms * (k > 0 ? k : 1);
+  if (grid > p.ntiles) grid = p.ntiles > 0 ? p.ntiles : 1;
+  k_batch<THREADS, CH><<<(unsigned)grid, THREADS, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool batch_shape_supported(int threads, int items) {
+  return (threads == 128 || threads == 256 || threads == 512) && (items == 8 || items == 16);
+}
+
+size_t batch_ws_bytes(int64_t ntiles, int nvec) {
+  return sizeof(WsHeader) + ((size_t)nvec * 4 + 15) / 16 * 16 + Slots<float>::bytes(ntiles) +
+         (size_t)ntiles * 4;
+}
+
+cudaError_t launch_batch(const BatchParams& p, const dr_tune& t, int sms, cudaStream_t s) {
+  if (p.ntiles <= 0) return cudaSuccess;
+  const int ch = t.items / 4;
+  if (t.threads == 128 && ch == 2) return go<128, 2>(p, t.ctas_per_sm, sms, s);
+  if (t.threads == 128 && ch == 4) return go<128, 4>(p, t.ctas_per_sm, sms, s);
+  if (t.threads == 256 && ch == 2) return go<256, 2>(p, t.ctas_per_sm, sms, s);
+  if (t.threads == 256 && ch == 4) return go<256, 4>(p, t.ctas_per_sm, sms, s);
+  if (t.threads == 512 && ch == 2) return go<512, 2>(p, t.ctas_per_sm, sms, s);
+  if (t.threads == 512 && ch == 4) return go<512, 4>(p, t.ctas_per_sm, sms, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace dr

@@ -1,0 +1,167 @@
+// for_each with a 5-point Jacobi update over a row-block segmented 2-D array
+// (Sec. 4.3 "for_each" over the block_row partition of Sec. 4.2.2), with the
+// halo exchange fused into the producing step, plus the stand-alone halo
+// exchange used before the first step.
+//
+// Layout: block k is one allocation of (rows_k + 2) x cols fp32, row 0 and row
+// rows_k + 1 being ghost copies of the neighbours' boundary rows.  A CTA owns
+// 4*TX columns x RB rows of one block and marches down its rows keeping the
+// rows above / at / below the current one in registers (each thread 4
+// consecutive columns as one float4), so every cell is read from HBM once per
+// step (plus 2 halo rows per RB rows) and written once: 8 B / cell / step.
+// West / east neighbours come from the adjacent lanes by warp shuffle; lanes 0
+// and 31 read the one missing column with a scalar load (an L1/L2 hit: the
+// neighbouring warp loads that line).  Rows are fetched G at a time so G
+// independent 16-byte loads per thread are in flight.  The epilogue also
+// writes a block's first / last own row into the neighbouring blocks' ghost
+// rows of the output, which is the halo exchange for the next step.
+//
+// Arithmetic (fixed order, no contraction): s = (N + S) + (W + E);
+// r = wn * s; and if wc != 0, r = r + wc * C.  Outside the grid is 0.
+#include "dr_device.cuh"
+
+namespace dr {
+namespace {
+
+constexpr int TX = kStencilThreads;
+constexpr int RB = kStencilRowsPerCta;
+constexpr int G = 8;  // rows fetched per group
+
+__device__ __forceinline__ int find_seg(const StencilParams& P, int64_t rb) {
+  int lo = 0, hi = P.nseg - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (P.seg[mid].rb_begin <= rb) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int VW>
+struct Row {
+  float v[VW];
+  float w, e;  // west of v[0] (lane 0 only), east of v[VW-1] (lane 31 only)
+};
+
+template <int VW>
+__device__ __forceinline__ void load_row(Row<VW>& r, const float* in, int64_t g, int64_t C, int64_t c,
+                                         bool zero_row, int lane) {
+  const bool act = c < C;
+  if (zero_row || !act) {
+#pragma unroll
+    for (int e = 0; e < VW; ++e) r.v[e] = 0.f;
+  } else if constexpr (VW == 4) {
+    V16<float> q = ld16<float>(in + g * C + c);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r.v[e] = q.v[e];
+  } else {
+    r.v[0] = __ldg(in + g * C + c);
+  }
+  r.w = 0.f;
+  r.e = 0.f;
+  if (!zero_row && act) {
+    if (lane == 0 && c > 0) r.w = __ldg(in + g * C + c - 1);
+    if (lane == 31 && c + VW < C) r.e = __ldg(in + g * C + c + VW);
+  }
+}
+
+template <int VW>
+__device__ __forceinline__ float upd(float n, float s, float w, float e, float ctr, float wc, float wn) {
+  const float sum = __fadd_rn(__fadd_rn(n, s), __fadd_rn(w, e));
+  float r = __fmul_rn(wn, sum);
+  if (wc != 0.f) r = __fadd_rn(r, __fmul_rn(wc, ctr));
+  return r;
+}
+
+template <int VW>
+__global__ void __launch_bounds__(TX) k_stencil5(const __grid_constant__ StencilParams P) {
+  const int s = find_seg(P, blockIdx.y);
+  const StencilSeg& S = P.seg[s];
+  const int64_t C = P.cols;
+  const int64_t r0 = 1 + ((int64_t)blockIdx.y - S.rb_begin) * RB;  // first own row (1-based)
+  const int64_t r1 = min(r0 + RB, S.rows + 1);                      // one past the last
+  const int lane = threadIdx.x & 31;
+  const int64_t c = ((int64_t)blockIdx.x * TX + threadIdx.x) * VW;
+  const bool act = c < C;
+  const bool top = s == 0, bot = s == P.nseg - 1;
+  const float wc = P.wc, wn = P.wn;
+
+  Row<VW> up, cur;
+  load_row<VW>(up, S.in, r0 - 1, C, c, top && r0 - 1 == 0, lane);
+  load_row<VW>(cur, S.in, r0, C, c, false, lane);
+
+  for (int64_t r = r0; r < r1; r += G) {
+    Row<VW> nx[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const int64_t g = r + 1 + k;
+      if (g <= r1) load_row<VW>(nx[k], S.in, g, C, c, bot && g == S.rows + 1, lane);
+    }
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const int64_t row = r + k;
+      if (row < r1) {
+        // west / east neighbours along the row
+        float wv = __shfl_up_sync(0xffffffffu, cur.v[VW - 1], 1);
+        float ev = __shfl_down_sync(0xffffffffu, cur.v[0], 1);
+        if (lane == 0) wv = cur.w;
+        if (lane == 31) ev = cur.e;
+        float o[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          const float W = e == 0 ? wv : cur.v[e - 1];
+          const float E = e == VW - 1 ? ev : cur.v[e + 1];
+          o[e] = upd<VW>(up.v[e], nx[k].v[e], W, E, cur.v[e], wc, wn);
+        }
+        if (act) {
+          float* dst = S.out + row * C + c;
+          // a block's first / last own row also goes to the neighbours' ghost rows
+          float* g_up = (row == 1 && S.out_prev) ? S.out_prev + (S.prev_rows + 1) * C + c : nullptr;
+          float* g_dn = (row == S.rows && S.out_next) ? S.out_next + c : nullptr;
+          if constexpr (VW == 4) {
+            V16<float> q;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) q.v[e] = o[e];
+            st16<float>(dst, q);
+            if (g_up) st16<float>(g_up, q);
+            if (g_dn) st16<float>(g_dn, q);
+          } else {
+            *dst = o[0];
+            if (g_up) *g_up = o[0];
+            if (g_dn) *g_dn = o[0];
+          }
+        }
+        up = cur;
+        cur = nx[k];
+      }
+    }
+  }
+}
+
+__global__ void k_halo(const __grid_constant__ HaloParams P) {
+  const auto& b = P.b[blockIdx.y];
+  const float* src = blockIdx.z == 0 ? b.src_last : b.src_first;
+  float* dst = blockIdx.z == 0 ? b.dst_top_ghost : b.dst_bot_ghost;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P.cols; j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = src[j];
+}
+
+}  // namespace
+
+cudaError_t launch_stencil(const StencilParams& p, cudaStream_t s) {
+  const int vw = p.vec_ok ? 4 : 1;
+  dim3 grid((unsigned)((p.cols + (int64_t)TX * vw - 1) / ((int64_t)TX * vw)), (unsigned)p.nrb);
+  if (p.vec_ok) k_stencil5<4><<<grid, TX, 0, s>>>(p);
+  else k_stencil5<1><<<grid, TX, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_halo(const HaloParams& p, cudaStream_t s) {
+  if (p.nbound <= 0) return cudaSuccess;
+  const int threads = 256;
+  unsigned gx = (unsigned)std::min<int64_t>((p.cols + threads - 1) / threads, 64);
+  k_halo<<<dim3(gx, p.nbound, 2), threads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace dr

@@ -1,0 +1,194 @@
+"""The C ABI without a GPU: the library loads, exports every entry point of
+include/dr.h, and its host-side logic (validation, index arithmetic, zip
+re-segmentation, take / drop) matches the oracle.  No call here touches the
+device: containers are built over fake (never dereferenced) pointers."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2406_00158_gb300 import _lib as L
+from paper_2406_00158_gb300 import build as B
+from paper_2406_00158_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "dr.h")).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(dr_\w+)\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(lib):
+    names = header_functions()
+    assert len(names) >= 35
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in L.PROTOTYPES, n
+    assert set(L.PROTOTYPES) == set(names)
+    assert lib.dr_version() == 1
+
+
+def fake_ptrs(lens, base=1 << 32, esz=4):
+    out, p = [], base
+    for n in lens:
+        out.append(p)
+        p += ((n * esz + 255) // 256 + 1) * 256
+    return out
+
+
+def make_vec(lens, dtype=L.DR_F32, ptrs=None):
+    ptrs = ptrs or fake_ptrs(lens)
+    h = ctypes.c_void_p()
+    rc = L.lib().dr_vec_create(dtype, len(lens), (ctypes.c_int64 * len(lens))(*lens),
+                               (ctypes.c_void_p * len(lens))(*ptrs), ctypes.byref(h))
+    return rc, h
+
+
+def test_vec_create_validation(lib):
+    rc, h = make_vec([4, 0, 5])
+    assert rc == L.DR_OK
+    n, ns, dt = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+    assert lib.dr_vec_info(h, ctypes.byref(dt), ctypes.byref(ns), ctypes.byref(n)) == 0
+    assert (dt.value, ns.value, n.value) == (L.DR_F32, 3, 9)
+    lib.dr_vec_destroy(h)
+    assert make_vec([3, -1])[0] == L.DR_E_INVAL
+    assert make_vec([3, 2], ptrs=[1 << 20, 0])[0] == L.DR_E_INVAL      # NULL non-empty segment
+    assert make_vec([3, 0], ptrs=[1 << 20, 0])[0] == L.DR_OK           # NULL empty segment is fine
+    assert make_vec([3], ptrs=[(1 << 20) + 2])[0] == L.DR_E_ALIGN     # not element aligned
+    assert make_vec([3], dtype=9)[0] == L.DR_E_DTYPE
+    h = ctypes.c_void_p()
+    assert lib.dr_vec_create(0, 0, None, None, ctypes.byref(h)) == L.DR_E_INVAL
+    assert "nseg" in L.last_error()
+
+
+def test_block_lengths_ceil_partition(lib):
+    for n, p in [(10, 3), (9, 3), (1, 4), (0, 2), (1 << 20, 8), (7, 7)]:
+        out = (ctypes.c_int64 * p)()
+        assert lib.dr_block_lengths(n, p, out) == 0
+        b = -(-n // p)
+        assert list(out) == inputs.block_segments(n, p)
+        assert sum(out) == n and all(v <= b for v in out)
+
+
+def test_locate_matches_bruteforce(lib):
+    lens = [3, 0, 5, 1, 0, 4]
+    _, h = make_vec(lens)
+    owner = [(k, j) for k, L_ in enumerate(lens) for j in range(L_)]
+    seg, off = ctypes.c_int(), ctypes.c_int64()
+    for i, (k, j) in enumerate(owner):
+        assert lib.dr_vec_locate(h, i, ctypes.byref(seg), ctypes.byref(off)) == 0
+        assert (seg.value, off.value) == (k, j)
+    assert lib.dr_vec_locate(h, len(owner), ctypes.byref(seg), ctypes.byref(off)) == L.DR_E_BOUNDS
+    assert lib.dr_vec_locate(h, -1, ctypes.byref(seg), ctypes.byref(off)) == L.DR_E_BOUNDS
+    lib.dr_vec_destroy(h)
+
+
+def view_of(h):
+    v = ctypes.c_void_p()
+    assert L.lib().dr_view_of(h, ctypes.byref(v)) == 0
+    return v
+
+
+def pieces(view):
+    n = ctypes.c_int()
+    size = ctypes.c_int64()
+    L.lib().dr_view_info(view, ctypes.byref(size), None, None, ctypes.byref(n))
+    arr = (L.dr_piece * max(1, n.value))()
+    assert L.lib().dr_view_segments(view, n.value, arr) == 0
+    return size.value, [(p.seg[0], p.off[0], p.seg[1], p.off[1], p.len) for p in arr[:n.value]]
+
+
+@pytest.mark.parametrize("trial", range(25))
+def test_zip_resegmentation_matches_oracle(lib, trial):
+    na, nb = 1 + trial % 6, 1 + (3 * trial) % 7
+    la = inputs.random_cut_segments(300 + trial, 120, na)
+    lb = inputs.random_cut_segments(400 + trial, 120 - (trial % 3) * 7, nb)
+    if trial % 4 == 0:
+        la = [0] + la + [0]
+    _, ha = make_vec(la)
+    _, hb = make_vec(lb, ptrs=fake_ptrs(lb, base=1 << 40))
+    z = ctypes.c_void_p()
+    assert lib.dr_view_zip(view_of(ha), view_of(hb), ctypes.byref(z)) == 0
+    size, got = pieces(z)
+    assert got == oracle.zip_segments_bruteforce(la, lb)
+    assert size == min(sum(la), sum(lb))
+
+
+def test_take_drop_trim_segments(lib):
+    lens = [5, 3, 0, 6]
+    _, h = make_vec(lens)
+    v = view_of(h)
+    for f in range(0, 15):
+        for l in range(0, 15):
+            t, d = ctypes.c_void_p(), ctypes.c_void_p()
+            assert lib.dr_view_drop(v, f, ctypes.byref(d)) == 0
+            assert lib.dr_view_take(d, l, ctypes.byref(t)) == 0
+            size, got = pieces(t)
+            lo = min(f, 14)
+            hi = min(14, lo + l)
+            assert size == hi - lo
+            # brute force: owners of [lo, hi) grouped by segment
+            owners = [(k, j) for k, L_ in enumerate(lens) for j in range(L_)][lo:hi]
+            exp = []
+            for k, j in owners:
+                if exp and exp[-1][0] == k:
+                    exp[-1][4] += 1
+                else:
+                    exp.append([k, j, -1, 0, 1])
+            assert [list(p) for p in got] == exp
+            lib.dr_view_destroy(t)
+            lib.dr_view_destroy(d)
+
+
+def test_view_composition_rules(lib):
+    _, ha = make_vec([8])
+    _, hb = make_vec([8], dtype=L.DR_F64, ptrs=[1 << 44])
+    va, vb = view_of(ha), view_of(hb)
+    z = ctypes.c_void_p()
+    assert lib.dr_view_zip(va, vb, ctypes.byref(z)) == L.DR_E_DTYPE
+    _, hc = make_vec([4, 4], ptrs=[1 << 41, 1 << 42])
+    assert lib.dr_view_zip(va, view_of(hc), ctypes.byref(z)) == 0
+    t = ctypes.c_void_p()
+    assert lib.dr_view_transform(z, L.DR_U_SCALE, 2.0, ctypes.byref(t)) == L.DR_E_INVAL  # raw zip
+    zt = ctypes.c_void_p()
+    assert lib.dr_view_zip_transform(z, L.DR_MUL, ctypes.byref(zt)) == 0
+    arity = ctypes.c_int()
+    lib.dr_view_info(zt, None, ctypes.byref(arity), None, None)
+    assert arity.value == 1
+    # chains are bounded
+    cur = zt
+    for k in range(4):
+        nxt = ctypes.c_void_p()
+        assert lib.dr_view_transform(cur, L.DR_U_ADD, 1.0, ctypes.byref(nxt)) == 0
+        cur = nxt
+    nxt = ctypes.c_void_p()
+    assert lib.dr_view_transform(cur, L.DR_U_ADD, 1.0, ctypes.byref(nxt)) == L.DR_E_UNSUPPORTED
+    # zip of a zip is outside this build
+    assert lib.dr_view_zip(zt, va, ctypes.byref(nxt)) == L.DR_E_UNSUPPORTED
+
+
+def test_md2_validation(lib):
+    h = ctypes.c_void_p()
+    rows = (ctypes.c_int64 * 2)(3, 4)
+    ptrs = (ctypes.c_void_p * 2)(1 << 32, 1 << 33)
+    assert lib.dr_md2_create(L.DR_F32, 7, 16, 2, rows, ptrs, ctypes.byref(h)) == 0
+    lib.dr_md2_destroy(h)
+    assert lib.dr_md2_create(L.DR_F32, 8, 16, 2, rows, ptrs, ctypes.byref(h)) == L.DR_E_INVAL
+    assert lib.dr_md2_create(L.DR_F64, 7, 16, 2, rows, ptrs, ctypes.byref(h)) == L.DR_E_DTYPE
+    bad = (ctypes.c_void_p * 2)(1 << 32, (1 << 33) + 2)
+    assert lib.dr_md2_create(L.DR_F32, 7, 16, 2, rows, bad, ctypes.byref(h)) == L.DR_E_ALIGN
+
+
+def test_status_knobs(lib):
+    assert lib.dr_set_spin_limit(0) == L.DR_E_INVAL
+    assert lib.dr_set_spin_limit(1 << 21) == 0
+    assert lib.dr_debug_skip_publish(-5) == 0

@@ -1,0 +1,221 @@
+"""inclusive / exclusive / reverse scan across segment boundaries on the GPU
+(single pass, decoupled lookback), through the C ABI, against the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_00158_gb300 import inputs
+from tests import gpu_util as G
+from tests import tolerances as T
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    G.dev()
+    from paper_2406_00158_gb300 import api
+    return api
+
+
+def scan_i64(api, x, lens, out_lens=None, offset=0):
+    vx = G.segvec(x, lens, offset_elems=offset)
+    out = G.empty_like_vec(out_lens or lens, torch.int64)
+    api.inclusive_scan(vx, out)
+    api.sync_status()
+    return G.to_np(out)
+
+
+def test_scan_i64_config_2p20_uneven_1_2_3_2(api):
+    """int64, n = 2^20, 4 segments 1:2:3:2, values U[0,1000): bit-exact."""
+    n = 1 << 20
+    lens = inputs.proportional_segments(n, [1, 2, 3, 2])
+    assert lens == [131072, 262144, 393216, 262144]
+    x = inputs.uniform_int64(inputs.SEED_SCAN_I64, n)
+    assert np.array_equal(scan_i64(api, x, lens), oracle.inclusive_scan_i64(x))
+
+
+@pytest.mark.parametrize("lens", [
+    [1 << 16], [1] * 64 + [(1 << 16) - 64], [0, 5, 0, 65_531, 0], [2047, 2049, 4096, 57_344],
+    "random", "random_unaligned_out",
+])
+def test_scan_i64_segment_split_invariance(api, lens):
+    n = 1 << 16
+    x = inputs.uniform_int64(31, n, 0, 1000)
+    out_lens = None
+    if lens == "random":
+        lens = inputs.random_cut_segments(7, n, 8)
+    elif lens == "random_unaligned_out":
+        lens = inputs.random_cut_segments(8, n, 5)
+        out_lens = inputs.random_cut_segments(9, n, 7)
+    assert np.array_equal(scan_i64(api, x, lens, out_lens), oracle.inclusive_scan_i64(x))
+
+
+def test_scan_i64_all_small_splits(api):
+    """Brute force over every split of n = 8 into up to 3 segments (empty allowed)."""
+    x = inputs.uniform_int64(37, 8, 0, 1000)
+    ref = oracle.inclusive_scan_i64(x)
+    for a in range(9):
+        for b in range(a, 9):
+            lens = [a, b - a, 8 - b]
+            lens = [l for l in lens] if sum(lens) == 8 else None
+            assert np.array_equal(scan_i64(api, x, lens), ref)
+
+
+def test_scan_i64_unaligned_and_closed_forms(api):
+    n = 100_003
+    x = inputs.uniform_int64(41, n, 0, 1000)
+    assert np.array_equal(scan_i64(api, x, [50_001, 50_002], offset=1), oracle.inclusive_scan_i64(x))
+    ones = np.ones(n, np.int64)
+    assert np.array_equal(scan_i64(api, ones, [3, n - 3]), np.arange(1, n + 1))
+
+
+def test_scan_i64_in_place(api):
+    n = 77_777
+    x = inputs.uniform_int64(43, n, 0, 1000)
+    lens = [30_000, 47_777]
+    v = G.segvec(x, lens)
+    api.inclusive_scan(v, v)
+    api.sync_status()
+    assert np.array_equal(G.to_np(v), oracle.inclusive_scan_i64(x))
+
+
+def test_scan_i64_full_size_roofline_case(api):
+    """int64 at n = 2^28 (4 GB per array) in 4 segments 1:2:3:2: bit-exact."""
+    n = 1 << 28
+    lens = inputs.proportional_segments(n, [1, 2, 3, 2])
+    x = inputs.uniform_int64(inputs.SEED_SCAN_I64, n)
+    got = scan_i64(api, x, lens)
+    assert np.array_equal(got, oracle.inclusive_scan_i64(x))
+
+
+def check_f32_scan(got, x, lens, tile=4096):
+    y, s = oracle.inclusive_scan_f32_f64(x)
+    err = np.abs(got.astype(np.float64) - y)
+    bound = T.scan_bound(s, G.tile_index(lens, tile))
+    assert np.all(err <= bound), (np.argmax(err - bound), err.max())
+    return err, s
+
+
+@pytest.mark.parametrize("n,lens", [(3 * 4096 + 5, None), (100_000, [1, 49_999, 0, 50_000])])
+def test_scan_f32_small(api, n, lens):
+    x = inputs.uniform_pm1_f32(47, n)
+    lens = lens or [n]
+    vx = G.segvec(x, lens)
+    out = G.empty_like_vec(lens, torch.float32)
+    api.inclusive_scan(vx, out)
+    api.sync_status()
+    check_f32_scan(G.to_np(out), x, lens)
+
+
+def test_scan_f32_exact_special_cases(api):
+    n = 1 << 20
+    lens = inputs.block_segments(n, 8)
+    ones = G.segvec(np.ones(n, np.float32), lens)
+    out = G.empty_like_vec(lens, torch.float32)
+    api.inclusive_scan(ones, out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), np.arange(1, n + 1, dtype=np.float32))
+    xi = inputs.uniform_int64(53, n, -8, 8).astype(np.float32)  # |prefix| < 2^24: exact
+    api.inclusive_scan(G.segvec(xi, lens), out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), np.cumsum(xi.astype(np.int64)).astype(np.float32))
+
+
+def test_scan_f32_full_size_8_segments(api):
+    """fp32 inclusive_scan over 2^28 elements in 8 segments (same x as the dot)."""
+    n = 1 << 28
+    x = inputs.uniform_pm1_f32(inputs.SEED_DOT_X, n)
+    lens = inputs.block_segments(n, 8)
+    vx = G.segvec(x, lens)
+    out = G.empty_like_vec(lens, torch.float32)
+    api.inclusive_scan(vx, out)
+    api.sync_status()
+    got = G.to_np(out)
+    err, s = check_f32_scan(got, x, lens)
+    seq = oracle.inclusive_scan_f32_seq(x)
+    y, _ = oracle.inclusive_scan_f32_f64(x)
+    seq_err = np.abs(seq.astype(np.float64) - y)
+    print(f"scan f32 2^28: max |err|/S = {np.max(err / np.maximum(s, 1e-30)):.3e}; "
+          f"max err {err.max():.3e} vs sequential fp32 {seq_err.max():.3e} "
+          f"(ratio {err.max() / max(seq_err.max(), 1e-30):.3f})")
+
+
+def test_exclusive_scan(api):
+    n = 60_001
+    xi = inputs.uniform_int64(59, n, 0, 1000)
+    lens = [20_000, 0, 40_001]
+    out = G.empty_like_vec(lens, torch.int64)
+    api.exclusive_scan(G.segvec(xi, lens), out, init=7)
+    api.sync_status()
+    exp = np.concatenate([[7], 7 + oracle.inclusive_scan_i64(xi)[:-1]])
+    assert np.array_equal(G.to_np(out), exp)
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_scan_max_min(api, op):
+    n = 50_000
+    x = inputs.uniform_pm1_f32(61, n)
+    lens = [17, 24_983, 25_000]
+    out = G.empty_like_vec(lens, torch.float32)
+    api.inclusive_scan(G.segvec(x, lens), out, op=op)
+    api.sync_status()
+    f = np.maximum.accumulate if op == "max" else np.minimum.accumulate
+    assert np.array_equal(G.to_np(out), f(x))
+
+
+def test_scan_over_fused_zip_transform(api):
+    """scan(zip(x, y) | multiply) in int64: no intermediate array."""
+    n = 40_000
+    x = inputs.uniform_int64(67, n, -30, 30)
+    y = inputs.uniform_int64(71, n, -30, 30)
+    vx, vy = G.segvec(x, [10_000, 30_000]), G.segvec(y, [25_000, 15_000])
+    out = G.empty_like_vec([n], torch.int64)
+    api.inclusive_scan(api.dot_view(vx, vy), out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), oracle.inclusive_scan_i64(x * y))
+
+
+def test_reverse_scan(api):
+    n = 123_457
+    g = inputs.uniform_pm1_f32(73, n)
+    lens = [100, 60_000, 63_357]
+    out = G.empty_like_vec(lens, torch.float32)
+    api.reverse_inclusive_scan(G.segvec(g, lens), out)
+    api.sync_status()
+    ref = oracle.reverse_inclusive_scan_f64(g.astype(np.float64))
+    absref = oracle.reverse_inclusive_scan_f64(np.abs(g).astype(np.float64))
+    tiles_from_end = G.tile_index(lens, 4096)
+    tiles_from_end = tiles_from_end.max() - tiles_from_end
+    err = np.abs(G.to_np(out).astype(np.float64) - ref)
+    assert np.all(err <= T.scan_bound(absref, tiles_from_end))
+    gi = inputs.uniform_int64(79, n, -100, 100)
+    out64 = G.empty_like_vec(lens, torch.int64)
+    api.reverse_inclusive_scan(G.segvec(gi, lens), out64)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out64), np.cumsum(gi[::-1])[::-1])
+
+
+def test_bounded_wait_reports_timeout_and_recovers(api):
+    """A tile that never publishes makes its successors' waits expire: the call
+    reports DR_E_TIMEOUT (no hang), and the next call is correct again."""
+    from paper_2406_00158_gb300 import _lib as L
+    n = 64 * 4096
+    x = inputs.uniform_int64(83, n, 0, 1000)
+    lens = [n]
+    vx = G.segvec(x, lens)
+    out = G.empty_like_vec(lens, torch.int64)
+    api.set_spin_limit(2000)
+    try:
+        api.debug_skip_publish(5)
+        api.inclusive_scan(vx, out)
+        with pytest.raises(L.DRError) as ei:
+            api.sync_status()
+        assert ei.value.status == L.DR_E_TIMEOUT
+    finally:
+        api.set_spin_limit(1 << 21)
+        api.debug_skip_publish(-1)
+    api.inclusive_scan(vx, out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), oracle.inclusive_scan_i64(x))
