@@ -205,7 +205,8 @@ def dot_view(x: SegmentedVector, y: SegmentedVector) -> View:
 
 
 def inclusive_scan(inp, out: SegmentedVector, op="plus", stream=None) -> SegmentedVector:
-    call("dr_inclusive_scan", _as_view(inp).handle, out.handle, _op(op), stream_handle(stream))
+    v = _as_view(inp)  # held for the duration of the call (its handle is freed with it)
+    call("dr_inclusive_scan", v.handle, out.handle, _op(op), stream_handle(stream))
     return out
 
 
@@ -217,7 +218,8 @@ def exclusive_scan(inp, out: SegmentedVector, init, op="plus", stream=None) -> S
 
 
 def reverse_inclusive_scan(inp, out: SegmentedVector, stream=None) -> SegmentedVector:
-    call("dr_reverse_inclusive_scan", _as_view(inp).handle, out.handle, stream_handle(stream))
+    v = _as_view(inp)
+    call("dr_reverse_inclusive_scan", v.handle, out.handle, stream_handle(stream))
     return out
 
 

@@ -56,6 +56,7 @@ __device__ __forceinline__ int wrap_mul(int a, int b) { return (int)((unsigned)a
 
 template <int OP>
 struct Op {
+  static constexpr int kOp = OP;
   template <typename T>
   static __device__ __forceinline__ T apply(T a, T b) {
     if constexpr (OP == DR_PLUS) return wrap_add(a, b);
@@ -166,6 +167,36 @@ __device__ __forceinline__ void st16(void* p, const V16<T>& o) {
                : "memory");
 }
 
+// L2 eviction-priority policies (createpolicy) and 128-bit accesses carrying them.
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+template <typename T>
+__device__ __forceinline__ V16<T> ld16_hint(const void* p, unsigned long long pol) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p), "l"(pol));
+  V16<T> o;
+  memcpy(&o, &r, 16);
+  return o;
+}
+template <typename T>
+__device__ __forceinline__ void st16_hint(void* p, const V16<T>& o, unsigned long long pol) {
+  uint4 r;
+  memcpy(&r, &o, 16);
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "r"(r.x), "r"(r.y),
+               "r"(r.z), "r"(r.w), "l"(pol)
+               : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ T ld1(const void* p) {
   return __ldg(reinterpret_cast<const T*>(p));
@@ -230,21 +261,28 @@ __device__ __forceinline__ T from_bits(unsigned long long u) {
 //             load the flag with acquire, then the value.
 // --------------------------------------------------------------------------
 constexpr unsigned kStateA = 1, kStateP = 2;
+// One slot per 128-byte line: hundreds of CTAs poll the slots just behind their
+// tiles, and packing 16 slots into a line turns those polls (and the publishers'
+// stores queued behind them) into an L2 hot spot.
+constexpr int kSlotBytes = 128;
 
 template <typename T, bool PACKED = (sizeof(T) == 4)>
 struct Slots;
 
 template <typename T>
-struct Slots<T, true> {
-  unsigned long long* w;
-  static __host__ __device__ size_t bytes(int64_t ntiles) { return (size_t)ntiles * 8; }
-  __device__ void bind(char* base, int64_t) { w = reinterpret_cast<unsigned long long*>(base); }
+struct Slots<T, true> {  // [flag:32 | value bits:32] in one 64-bit word
+  char* base;
+  static __host__ __device__ size_t bytes(int64_t ntiles) { return (size_t)ntiles * kSlotBytes; }
+  __device__ void bind(char* b, int64_t) { base = b; }
+  __device__ __forceinline__ unsigned long long* word(int64_t i) const {
+    return reinterpret_cast<unsigned long long*>(base + i * kSlotBytes);
+  }
   __device__ __forceinline__ void publish(int64_t i, unsigned tag, unsigned state, T v) {
-    st_relaxed_u64(w + i, ((unsigned long long)(tag | state) << 32) | to_bits(v));
+    st_relaxed_u64(word(i), ((unsigned long long)(tag | state) << 32) | to_bits(v));
   }
   // returns the state (0 if not yet valid for this epoch)
   __device__ __forceinline__ unsigned poll(int64_t i, unsigned tag, T& v) const {
-    unsigned long long x = ld_relaxed_u64(w + i);
+    unsigned long long x = ld_relaxed_u64(word(i));
     unsigned f = (unsigned)(x >> 32);
     if ((f & ~3u) != tag) return 0;
     v = from_bits<T>(x & 0xffffffffull);
@@ -253,30 +291,25 @@ struct Slots<T, true> {
 };
 
 template <typename T>
-struct Slots<T, false> {
-  unsigned* flag;
-  T* agg;
-  T* pfx;
-  static __host__ __device__ size_t bytes(int64_t ntiles) {
-    return ((size_t)ntiles * 4 + 15) / 16 * 16 + (size_t)ntiles * 16;
+struct Slots<T, false> {  // {flag, pad, aggregate, inclusive prefix}; flag released after the value
+  char* base;
+  static __host__ __device__ size_t bytes(int64_t ntiles) { return (size_t)ntiles * kSlotBytes; }
+  __device__ void bind(char* b, int64_t) { base = b; }
+  __device__ __forceinline__ unsigned* flag(int64_t i) const {
+    return reinterpret_cast<unsigned*>(base + i * kSlotBytes);
   }
-  __device__ void bind(char* base, int64_t ntiles) {
-    flag = reinterpret_cast<unsigned*>(base);
-    agg = reinterpret_cast<T*>(base + ((size_t)ntiles * 4 + 15) / 16 * 16);
-    pfx = agg + ntiles;
+  __device__ __forceinline__ unsigned long long* val(int64_t i, unsigned state) const {
+    return reinterpret_cast<unsigned long long*>(base + i * kSlotBytes + (state == kStateP ? 16 : 8));
   }
   __device__ __forceinline__ void publish(int64_t i, unsigned tag, unsigned state, T v) {
-    unsigned long long* dst = reinterpret_cast<unsigned long long*>(state == kStateP ? pfx + i : agg + i);
-    st_relaxed_u64(dst, to_bits(v));
-    st_release_u32(flag + i, tag | state);
+    st_relaxed_u64(val(i, state), to_bits(v));
+    st_release_u32(flag(i), tag | state);
   }
   __device__ __forceinline__ unsigned poll(int64_t i, unsigned tag, T& v) const {
-    unsigned f = ld_acquire_u32(flag + i);
+    unsigned f = ld_acquire_u32(flag(i));
     if ((f & ~3u) != tag) return 0;
-    unsigned s = f & 3u;
-    const unsigned long long* src =
-        reinterpret_cast<const unsigned long long*>(s == kStateP ? pfx + i : agg + i);
-    v = from_bits<T>(ld_relaxed_u64(src));
+    const unsigned s = f & 3u;
+    v = from_bits<T>(ld_relaxed_u64(val(i, s)));
     return s;
   }
 };
@@ -294,10 +327,12 @@ __device__ __forceinline__ unsigned wait_slot(const S& slots, int64_t i, unsigne
                                               int64_t limit, unsigned* status) {
   unsigned s = slots.poll(i, tag, v);
   if (s) return s;
-  unsigned ns = 32;
+  unsigned ns = 16;
   for (int64_t polls = 1;; ++polls) {
-    __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
+    if (polls > 4) {  // the predecessor is usually a few hundred ns away: spin first
+      __nanosleep(ns);
+      if (ns < 512) ns <<= 1;
+    }
     s = slots.poll(i, tag, v);
     if (s) return s;
     if (polls >= limit) {
@@ -308,6 +343,54 @@ __device__ __forceinline__ unsigned wait_slot(const S& slots, int64_t i, unsigne
   }
   v = OPT::template identity<T>();
   return kStateP;
+}
+
+// --------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk, 1-D: 16-byte aligned addresses, size a
+// multiple of 16) completing on a shared-memory mbarrier
+// --------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for an mbarrier phase; records DR_E_TIMEOUT and returns false on expiry.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int64_t limit,
+                                          unsigned* status) {
+  for (int64_t k = 0; k < limit; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+  raise_status(status, DR_E_TIMEOUT, 0xffffffffu);
+  return false;
 }
 
 // --------------------------------------------------------------------------
@@ -334,6 +417,63 @@ __device__ __forceinline__ T warp_inclusive(T v, int lane) {
     }
   }
   return v;
+}
+
+// --------------------------------------------------------------------------
+// Warp-wide decoupled lookback.  Returns the combination of the published
+// values of tiles (pred, pred-1, ...) down to and including the nearest one in
+// the inclusive-prefix state; tiles before `lo` count as an inclusive prefix
+// equal to the identity.  Each round polls G slots per lane (32*G tiles, nearest
+// first: lane l holds pred - l*G - g), waits only for unpublished slots nearer
+// than the nearest inclusive prefix, and moves on by 32*G if there is none.
+// One round costs one L2 round trip; covering 32*G tiles per round keeps the
+// walk short even when hundreds of tiles are in flight.
+// --------------------------------------------------------------------------
+template <typename T, typename OPT, int G, typename S>
+__device__ __forceinline__ T lookback(const S& slots, int64_t pred, int64_t lo, unsigned tag, int lane,
+                                      int64_t limit, unsigned* status) {
+  const T ident = OPT::template identity<T>();
+  T run = ident;
+  while (true) {
+    T val[G];
+    unsigned st[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t i = pred - (int64_t)(lane * G + g);
+      val[g] = ident;
+      st[g] = kStateP;
+      if (i >= lo) st[g] = slots.poll(i, tag, val[g]);
+    }
+    int gp = G;  // this lane's nearest inclusive prefix
+#pragma unroll
+    for (int g = G - 1; g >= 0; --g)
+      if (st[g] == kStateP) gp = g;
+    unsigned pm = __ballot_sync(0xffffffffu, gp < G);
+    int fl = pm ? __ffs(pm) - 1 : 32;
+    if (lane <= fl) {
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (st[g] == 0 && (lane < fl || g < gp)) {
+          const int64_t i = pred - (int64_t)(lane * G + g);
+          st[g] = wait_slot<T, S, OPT>(slots, i, tag, val[g], limit, status);
+        }
+    }
+    __syncwarp();
+    gp = G;
+#pragma unroll
+    for (int g = G - 1; g >= 0; --g)
+      if (st[g] == kStateP) gp = g;
+    pm = __ballot_sync(0xffffffffu, gp < G);
+    fl = pm ? __ffs(pm) - 1 : 32;
+    T c = ident;
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (lane < fl || (lane == fl && g <= gp)) c = OPT::apply(c, val[g]);
+    run = OPT::apply(warp_reduce<T, OPT::kOp>(c), run);
+    if (pm) break;
+    pred -= 32 * G;
+  }
+  return run;
 }
 
 }  // namespace dr

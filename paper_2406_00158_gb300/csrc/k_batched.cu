@@ -141,25 +141,7 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
         if (lane == 0) slots.publish(t, tag, kStateP, agg);
       } else {
         if (lane == 0) slots.publish(t, tag, kStateA, agg);
-        int64_t pred = t - 1;
-        float run = 0.f;
-        while (true) {
-          const int64_t i = pred - lane;
-          float val = 0.f;
-          unsigned st = kStateP;  // before the vector's first tile: identity
-          if (i >= first) st = slots.poll(i, tag, val);
-          unsigned pm = __ballot_sync(0xffffffffu, st == kStateP);
-          const int lim = pm ? __ffs(pm) - 1 : 32;
-          if (st == 0 && lane < lim)
-            st = wait_slot<float, Slots<float>, O>(slots, i, tag, val, P.spin_limit, P.status);
-          __syncwarp();
-          pm = __ballot_sync(0xffffffffu, st == kStateP);
-          const int fl = pm ? __ffs(pm) - 1 : 31;
-          const float w = warp_reduce<float, DR_PLUS>(lane <= fl ? val : 0.f);
-          run = w + run;
-          if (pm) break;
-          pred -= 32;
-        }
+        const float run = lookback<float, O, 4>(slots, t - 1, first, tag, lane, P.spin_limit, P.status);
         prefix = run;
         if (lane == 0) slots.publish(t, tag, kStateP, prefix + agg);
       }
