@@ -236,6 +236,26 @@ int dr_reverse_inclusive_scan(const dr_view* in, dr_vec* out, dr_stream_t stream
 int dr_transform_reduce(const dr_view* in, int op, const void* init, void* dev_result,
                         dr_stream_t stream);
 
+/* The dot product of dr_transform_reduce(zip(x, y) | DR_MUL, DR_PLUS) for callers
+ * that cannot allocate device memory at the call (a framework that owns all device
+ * memory through its own pool; a latency-critical loop that cannot pay for
+ * cudaMalloc, or for the device-wide synchronization of cudaFree).  The paper has
+ * no counterpart: this is an allocation-free variant of the same reduce kernel.
+ * x and y share one segmentation: segment k has lens[k] >= 0 fp32 elements at
+ * x_segs[k] and y_segs[k] (device pointers, 4-byte aligned; 16-byte aligned for
+ * 128-bit access; host arrays of nseg entries, 1 <= nseg <= 128).
+ * *dev_result = init + sum_i x_i*y_i (one device fp32).  Its scratch (32,832
+ * bytes: a counter header and one partial per CTA) is a fixed device array of
+ * the library, present on every device that loads it until the process exits;
+ * nothing is allocated.  The first call on a device looks up that array's
+ * device address (make it before any stream capture).  Every call shares the
+ * array: each clears its counter header on `stream` first, and calls that can
+ * overlap on the GPU race.  DR_E_UNSUPPORTED if nseg > 128 or the device needs
+ * more than 4096 CTAs' partials. */
+int dr_dot_f32_noalloc(int nseg, const int64_t* lens, const float* const* x_segs,
+                       const float* const* y_segs, float init, float* dev_result,
+                       dr_stream_t stream);
+
 /* Adjoint of d = <x, y> (dot product): gx = g * y and gy = g * x elementwise,
  * with g read from device memory (dev_g, one fp32).  Either output may be
  * NULL.  fp32 vectors of equal length; segmentations may differ. */

@@ -81,6 +81,7 @@ PROTOTYPES = {
     "dr_reverse_inclusive_scan": (_I, [_P, _P, _P]),
     "dr_transform_reduce": (_I, [_P, _I, _P, _P, _P]),
     "dr_scale_by_partner": (_I, [_P, _P, _P, _P, _P, _P]),
+    "dr_dot_f32_noalloc": (_I, [_I, _PI64, _PP, _PP, ctypes.c_float, _P, _P]),
     "dr_stencil5": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "dr_stencil5_T": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "dr_batch_plan": (_I, [_I, _PP, _PP, _PP, _P, ctypes.POINTER(dr_tune), _PP]),
