@@ -280,6 +280,17 @@ int dr_stencil5(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, doub
 int dr_stencil5_T(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
                   dr_stream_t stream);
 
+/* One backward step of the stencil chain that also yields the gradients of
+ * the weights.  With u_t = wc*u_{t-1} + wn*N(u_{t-1}) (N = sum of the 4
+ * neighbours) and in = u_bar_t (the gradient w.r.t. u_t): out = A^T in
+ * (= u_bar_{t-1}), and, with prev = the forward state u_{t-1},
+ *   dev_acc[0] += <u_bar_t, u_{t-1}>      (dL/dwc contribution of step t)
+ *   dev_acc[1] += <N(u_bar_t), u_{t-1}>   (dL/dwn contribution; N is symmetric)
+ * accumulated in FP64 (fp32 per-thread partials, one FP64 atomic per CTA and
+ * accumulator).  prev's ghost rows are not read.  dev_acc: 2 device doubles. */
+int dr_stencil5_T_wgrad(dr_md2* in, dr_md2* out, const dr_md2* prev, double wc, double wn,
+                        double* dev_acc, dr_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Batched execution: many independent segmented vectors in one launch        */
 /* ------------------------------------------------------------------------ */

@@ -84,6 +84,7 @@ PROTOTYPES = {
     "dr_dot_f32_noalloc": (_I, [_I, _PI64, _PP, _PP, ctypes.c_float, _P, _P]),
     "dr_stencil5": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "dr_stencil5_T": (_I, [_P, _P, _P, _I, _D, _D, _P]),
+    "dr_stencil5_T_wgrad": (_I, [_P, _P, _P, _D, _D, _P, _P]),
     "dr_batch_plan": (_I, [_I, _PP, _PP, _PP, _P, ctypes.POINTER(dr_tune), _PP]),
     "dr_batch_destroy": (_I, [_P]),
     "dr_batch_set_tune": (_I, [_P, ctypes.POINTER(dr_tune)]),

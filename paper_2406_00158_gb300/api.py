@@ -133,6 +133,39 @@ class SegmentedVector:
             L._lib.dr_vec_destroy(h)
 
 
+def packed_vectors(flat, shapes: Sequence[Sequence[int]], device="cuda", dtype=torch.float32):
+    """Many segmented vectors in one device buffer: vector v has segments
+    shapes[v] (element counts) taken in order from the flat host array `flat`
+    (None: uninitialized).  Every segment starts on a 16-byte boundary of the
+    buffer (128-bit access); the buffer is filled with one host-to-device copy.
+    Returns the list of SegmentedVector (each keeps the buffer alive)."""
+    esz = torch.empty((), dtype=dtype).element_size()
+    align = 16 // esz
+    offs, pos = [], 0
+    for sh in shapes:
+        o = []
+        for n in sh:
+            o.append(pos)
+            pos += (int(n) + align - 1) // align * align
+        offs.append(o)
+    buf = torch.empty(max(pos, 1), dtype=dtype, device=device)
+    if flat is not None:
+        src = torch.as_tensor(flat).reshape(-1)
+        host = torch.zeros(max(pos, 1), dtype=dtype)
+        k = 0
+        for sh, o in zip(shapes, offs):
+            for n, p0 in zip(sh, o):
+                host[p0:p0 + n] = src[k:k + n]
+                k += n
+        buf.copy_(host.pin_memory() if device != "cpu" else host)
+    vecs = []
+    for sh, o in zip(shapes, offs):
+        v = SegmentedVector([buf[p0:p0 + int(n)] for n, p0 in zip(sh, o)])
+        v._buffer = buf
+        vecs.append(v)
+    return vecs
+
+
 class View:
     """A lazy view (Sec. 4.4); its kernels fuse it into their loads."""
 
@@ -297,6 +330,15 @@ def stencil5_T(inp: MdArray, out: MdArray, tmp: Optional[MdArray], steps: int, w
                wn: float = 0.25, stream=None) -> MdArray:
     call("dr_stencil5_T", inp.handle, out.handle, tmp.handle if tmp is not None else None, int(steps),
          float(wc), float(wn), stream_handle(stream))
+    return out
+
+
+def stencil5_T_wgrad(inp: MdArray, out: MdArray, prev: MdArray, acc: torch.Tensor, wc: float = 0.0,
+                     wn: float = 0.25, stream=None) -> MdArray:
+    """out = A^T inp; acc[0] += <inp, prev>, acc[1] += <N(inp), prev> (acc: 2 fp64 on device)."""
+    assert acc.dtype == torch.float64 and acc.numel() >= 2 and acc.is_contiguous()
+    call("dr_stencil5_T_wgrad", inp.handle, out.handle, prev.handle, float(wc), float(wn),
+         ctypes.c_void_p(acc.data_ptr()), stream_handle(stream))
     return out
 
 

@@ -702,7 +702,7 @@ extern "C" int dr_scale_by_partner(const dr_vec* x, const dr_vec* y, const float
 }
 
 static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
-                      cudaStream_t s) {
+                      cudaStream_t s, const dr_md2* prev = nullptr, double* acc = nullptr) {
   clear_error();
   if (!in || !out) return fail(DR_E_INVAL, "%s: NULL array", who);
   if (steps < 1) return fail(DR_E_INVAL, "%s: steps must be >= 1", who);
@@ -712,6 +712,8 @@ static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int
   };
   if (!same(out) || (tmp && !same(tmp))) return fail(DR_E_INVAL, "%s: arrays differ in shape or blocking", who);
   if (in == out || in == tmp || out == tmp) return fail(DR_E_INVAL, "%s: in, out, tmp must be distinct", who);
+  if (acc && (!prev || !same(prev) || steps != 1))
+    return fail(DR_E_INVAL, "%s: needs one step and a forward state of the same shape", who);
   for (size_t k = 0; k < in->ptr.size(); ++k)
     if (out->ptr[k] == in->ptr[k] || (tmp && (tmp->ptr[k] == in->ptr[k] || tmp->ptr[k] == out->ptr[k])))
       return fail(DR_E_INVAL, "%s: in, out, tmp share storage", who);
@@ -722,7 +724,7 @@ static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int
   if (int r = exchange_halos(in, s)) return r;
   static thread_local StencilParams p;
   bool vec = in->cols % 4 == 0;
-  for (const dr_md2* m : {in, out, tmp})
+  for (const dr_md2* m : {(const dr_md2*)in, (const dr_md2*)out, (const dr_md2*)tmp, prev})
     if (m)
       for (char* q : m->ptr) vec = vec && (uintptr_t)q % 16 == 0;
   const dr_md2* src = in;
@@ -735,10 +737,12 @@ static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int
     p.wc = (float)wc;
     p.wn = (float)wn;
     p.vec_ok = vec ? 1 : 0;
+    p.acc = acc;
     int64_t rb = 0;
     for (int k = 0; k < nseg; ++k) {
       StencilSeg& g = p.seg[k];
       g.in = reinterpret_cast<const float*>(src->ptr[k]);
+      g.prev = prev ? reinterpret_cast<const float*>(prev->ptr[k]) : nullptr;
       g.out = reinterpret_cast<float*>(dst->ptr[k]);
       g.out_prev = k > 0 ? reinterpret_cast<float*>(dst->ptr[k - 1]) : nullptr;
       g.out_next = k + 1 < nseg ? reinterpret_cast<float*>(dst->ptr[k + 1]) : nullptr;
@@ -764,4 +768,12 @@ extern "C" int dr_stencil5(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, doub
 extern "C" int dr_stencil5_T(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
                              dr_stream_t stream) {
   return do_stencil("dr_stencil5_T", in, out, tmp, steps, wc, wn, (cudaStream_t)stream);
+}
+
+// One backward step of the stencil chain with the gradients of the weights:
+// out = A^T in, acc[0] += <in, prev>, acc[1] += <N(in), prev>.
+extern "C" int dr_stencil5_T_wgrad(dr_md2* in, dr_md2* out, const dr_md2* prev, double wc, double wn,
+                                   double* dev_acc, dr_stream_t stream) {
+  if (!dev_acc || (uintptr_t)dev_acc % 8) return fail(DR_E_INVAL, "dr_stencil5_T_wgrad: bad accumulator pointer");
+  return do_stencil("dr_stencil5_T_wgrad", in, out, nullptr, 1, wc, wn, (cudaStream_t)stream, prev, dev_acc);
 }

@@ -99,6 +99,7 @@ struct ScaleParams {  // dot adjoint: gx = g*y, gy = g*x
 
 struct StencilSeg {
   const float* in;   // allocation incl. ghost rows: (rows + 2) * cols
+  const float* prev; // weight-gradient step only: the forward state u_{t-1} (same layout)
   float* out;
   float* out_prev;   // output allocation of the block above (NULL for the first)
   float* out_next;   // output allocation of the block below (NULL for the last)
@@ -113,6 +114,7 @@ struct StencilParams {
   int64_t nrb;       // total row blocks
   float wc, wn;
   int vec_ok;        // cols % 4 == 0 and all pointers 16-byte aligned
+  double* acc;       // weight-gradient step only: acc[0] += <in, prev>, acc[1] += <N(in), prev>
   StencilSeg seg[kMaxPieces];
 };
 

@@ -73,7 +73,12 @@ __device__ __forceinline__ float upd(float n, float s, float w, float e, float c
   return r;
 }
 
-template <int VW>
+// WGRAD: the backward step of the weight gradients.  `in` holds u_bar_t, the
+// output is u_bar_{t-1} = A^T u_bar_t (= A u_bar_t), and with the forward state
+// u_{t-1} read from `prev` the kernel also accumulates <u_bar_t, u_{t-1}> (the
+// wc term) and <N(u_bar_t), u_{t-1}> (the wn term; N = neighbour sum, and
+// <u_bar, N u> = <N u_bar, u> because N is symmetric) into acc[0], acc[1].
+template <int VW, bool WGRAD>
 __global__ void __launch_bounds__(TX) k_stencil5(const __grid_constant__ StencilParams P) {
   const int s = find_seg(P, blockIdx.y);
   const StencilSeg& S = P.seg[s];
@@ -86,6 +91,7 @@ __global__ void __launch_bounds__(TX) k_stencil5(const __grid_constant__ Stencil
   const bool top = s == 0, bot = s == P.nseg - 1;
   const float wc = P.wc, wn = P.wn;
 
+  float gwc = 0.f, gwn = 0.f;  // weight-gradient partials (WGRAD)
   Row<VW> up, cur;
   load_row<VW>(up, S.in, r0 - 1, C, c, top && r0 - 1 == 0, lane);
   load_row<VW>(cur, S.in, r0, C, c, false, lane);
@@ -107,11 +113,31 @@ __global__ void __launch_bounds__(TX) k_stencil5(const __grid_constant__ Stencil
         if (lane == 0) wv = cur.w;
         if (lane == 31) ev = cur.e;
         float o[VW];
+        float pv[VW];
+        if constexpr (WGRAD) {
+          if (act) {
+            if constexpr (VW == 4) {
+              const V16<float> q = ld16<float>(S.prev + row * C + c);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) pv[e] = q.v[e];
+            } else {
+              pv[0] = __ldg(S.prev + row * C + c);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) pv[e] = 0.f;
+          }
+        }
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
           const float W = e == 0 ? wv : cur.v[e - 1];
           const float E = e == VW - 1 ? ev : cur.v[e + 1];
           o[e] = upd<VW>(up.v[e], nx[k].v[e], W, E, cur.v[e], wc, wn);
+          if constexpr (WGRAD) {
+            const float nsum = __fadd_rn(__fadd_rn(up.v[e], nx[k].v[e]), __fadd_rn(W, E));
+            gwc = __fmaf_rn(cur.v[e], pv[e], gwc);
+            gwn = __fmaf_rn(nsum, pv[e], gwn);
+          }
         }
         if (act) {
           float* dst = S.out + row * C + c;
@@ -136,6 +162,26 @@ __global__ void __launch_bounds__(TX) k_stencil5(const __grid_constant__ Stencil
       }
     }
   }
+  if constexpr (WGRAD) {
+    __shared__ float s_g[2][TX / 32];
+    gwc = warp_reduce<float, DR_PLUS>(gwc);
+    gwn = warp_reduce<float, DR_PLUS>(gwn);
+    if (lane == 0) {
+      s_g[0][threadIdx.x >> 5] = gwc;
+      s_g[1][threadIdx.x >> 5] = gwn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int w = 0; w < TX / 32; ++w) {
+        a += s_g[0][w];
+        b += s_g[1][w];
+      }
+      atomicAdd(P.acc, a);
+      atomicAdd(P.acc + 1, b);
+    }
+  }
 }
 
 __global__ void k_halo(const __grid_constant__ HaloParams P) {
@@ -151,8 +197,13 @@ __global__ void k_halo(const __grid_constant__ HaloParams P) {
 cudaError_t launch_stencil(const StencilParams& p, cudaStream_t s) {
   const int vw = p.vec_ok ? 4 : 1;
   dim3 grid((unsigned)((p.cols + (int64_t)TX * vw - 1) / ((int64_t)TX * vw)), (unsigned)p.nrb);
-  if (p.vec_ok) k_stencil5<4><<<grid, TX, 0, s>>>(p);
-  else k_stencil5<1><<<grid, TX, 0, s>>>(p);
+  if (p.acc) {
+    if (p.vec_ok) k_stencil5<4, true><<<grid, TX, 0, s>>>(p);
+    else k_stencil5<1, true><<<grid, TX, 0, s>>>(p);
+  } else {
+    if (p.vec_ok) k_stencil5<4, false><<<grid, TX, 0, s>>>(p);
+    else k_stencil5<1, false><<<grid, TX, 0, s>>>(p);
+  }
   return cudaGetLastError();
 }
 

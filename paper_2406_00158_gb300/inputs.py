@@ -38,7 +38,9 @@ SEED_DOT_X = 2407
 SEED_DOT_Y = 2408
 SEED_STENCIL = 2409
 SEED_GRAD = 2410
-SEED_BATCH = 2411
+SEED_BATCH = 2411     # batch shapes
+SEED_BATCH_X = 3411   # batch values x
+SEED_BATCH_P = 4411   # batch partner values p
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:

@@ -1,0 +1,113 @@
+"""Batched execution: thousands of independent segmented vectors, y_v =
+inclusive_scan(x_v) and dots[v] = <x_v, p_v> in one persistent launch (and its
+CUDA-graph replay), against the oracle per vector and against the
+one-launch-per-range baseline; the autotuner and its cache."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_00158_gb300 import inputs
+from tests import gpu_util as G
+from tests import tolerances as T
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    G.dev()
+    from paper_2406_00158_gb300 import api
+    return api
+
+
+def build(api, shapes, pshapes=None, seed=0):
+    tot = sum(map(sum, shapes))
+    x = inputs.uniform_pm1_f32(inputs.SEED_BATCH_X + seed, tot)
+    p = inputs.uniform_pm1_f32(inputs.SEED_BATCH_P + seed, tot)
+    xs = api.packed_vectors(x, shapes)
+    ps = api.packed_vectors(p, pshapes or shapes)
+    ys = api.packed_vectors(None, shapes)
+    dots = torch.full((len(shapes),), float("nan"), dtype=torch.float32, device="cuda")
+    return x, p, xs, ps, ys, dots
+
+
+def check(x, p, shapes, ys, dots, tile=4096):
+    off = 0
+    dh = dots.cpu().numpy()
+    for v, sh in enumerate(shapes):
+        n = sum(sh)
+        xv, pv = x[off:off + n], p[off:off + n]
+        off += n
+        y = ys[v].to_tensor().cpu().numpy()
+        yr, s = oracle.inclusive_scan_f32_f64(xv)
+        assert np.all(np.abs(y - yr) <= T.scan_bound(s, G.tile_index(sh, tile))), v
+        d, ad = oracle.dot_f64(xv, pv)
+        assert abs(dh[v] - d) <= T.gamma(-(-n // tile) + 64) * ad, (v, dh[v], d)
+
+
+def small_shapes():
+    shapes = [[1000], [1], [3, 5], [4096], [4097, 1], [10_000, 7, 1, 20_000], [8191, 8193],
+              [2] * 8, [123_457], [0, 5000, 0], [0]]
+    return shapes + inputs.batch_shapes(inputs.SEED_BATCH + 7, 40, lo=1e3, hi=2e5)
+
+
+@pytest.mark.parametrize("tune", [None, (128, 16, 4), (256, 8, 2), (512, 16, 1)])
+def test_batch_small_vs_oracle_repeat_graph_per_range(api, tune):
+    shapes = small_shapes()
+    x, p, xs, ps, ys, dots = build(api, shapes)
+    b = api.Batch(xs, ps, ys, dots, tune=tune)
+    for _ in range(2):  # self-cleaning workspace: a second launch is right too
+        dots.fill_(float("nan"))
+        b.run()
+        api.sync_status()
+        check(x, p, shapes, ys, dots, tile=b.tune[0] * b.tune[1])
+    dots.fill_(float("nan"))
+    b.run_graph()
+    b.run_graph()
+    api.sync_status()
+    check(x, p, shapes, ys, dots, tile=b.tune[0] * b.tune[1])
+    dots.fill_(float("nan"))
+    b.run_per_range()
+    api.sync_status()
+    check(x, p, shapes, ys, dots, tile=8192)
+
+
+def test_batch_non_aligned_partner(api):
+    shapes = small_shapes()
+    pshapes = [inputs.random_cut_segments(900 + v, sum(sh), 1 + v % 5) for v, sh in enumerate(shapes)]
+    x, p, xs, ps, ys, dots = build(api, shapes, pshapes, seed=1)
+    b = api.Batch(xs, ps, ys, dots)
+    b.run()
+    api.sync_status()
+    check(x, p, shapes, ys, dots)
+
+
+def test_batch_full_config_4096_vectors(api):
+    """4096 vectors, lengths log-uniform in [1e3, 1e6], 1-8 segments each."""
+    shapes = inputs.batch_shapes(inputs.SEED_BATCH, 4096)
+    x, p, xs, ps, ys, dots = build(api, shapes)
+    b = api.Batch(xs, ps, ys, dots)
+    b.run_graph()
+    api.sync_status()
+    check(x, p, shapes, ys, dots, tile=b.tune[0] * b.tune[1])
+
+
+def test_autotune_and_cache(api, tmp_path):
+    shapes = inputs.batch_shapes(inputs.SEED_BATCH + 99, 256, lo=1e3, hi=1e5)
+    x, p, xs, ps, ys, dots = build(api, shapes, seed=2)
+    b = api.Batch(xs, ps, ys, dots)
+    cache = str(tmp_path / "tune.json")
+    chosen = b.autotune(retune=True, cache_path=cache)
+    assert chosen[0] in (128, 256, 512) and chosen[1] in (8, 16) and 1 <= chosen[2] <= 8
+    assert b.tune == chosen
+    text = open(cache).read()
+    assert '"threads": %d' % chosen[0] in text
+    b.tune = (256, 8, 1)
+    assert b.autotune(retune=False, cache_path=cache) == chosen  # served from the cache
+    dots.fill_(float("nan"))
+    b.run()
+    api.sync_status()
+    check(x, p, shapes, ys, dots, tile=chosen[0] * chosen[1])
