@@ -195,8 +195,126 @@ def run_reference(args) -> None:
 # ------------------------------------------------------------------------------------------
 # the other hot-path rows (each timed with CUDA events on the launching stream)
 # ------------------------------------------------------------------------------------------
+def _time(fn, s, reps, flush=None):
+    """Mean ms per call over `reps` calls, CUDA events on stream s (flush between calls
+    if given, outside the measured interval)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        fn()
+        b.record(s)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def _row(ms, nbytes, peak, **kw):
+    gbs = nbytes / (ms / 1e3) / 1e9
+    d = {"ms": ms, "GB/s": gbs, "frac_of_peak": gbs / peak, "bytes": nbytes}
+    d.update(kw)
+    return d
+
+
 def measure_rows(api, dev, s, peak) -> dict:
-    return {}
+    """The other hot-path rows, each on its own workload."""
+    import torch
+    from paper_2406_00158_gb300 import autograd as AG
+    rows = {}
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flushbuf = torch.empty(4 * l2 // 4, dtype=torch.float32, device=dev)
+    flush = lambda: flushbuf.zero_()
+
+    # int64 inclusive_scan, 2^20 in 4 segments 1:2:3:2 (16.8 MB: L2-resident), and 2^28
+    for n, name in ((1 << 20, "int64_scan_2^20_1:2:3:2"), (1 << 28, "int64_scan_2^28_1:2:3:2")):
+        lens = inputs.proportional_segments(n, [1, 2, 3, 2])
+        x = inputs.uniform_int64(inputs.SEED_SCAN_I64, n)
+        vx = api.SegmentedVector.from_tensor(torch.from_numpy(x).to(dev), lens)
+        vo = api.SegmentedVector.empty(lens, torch.int64, dev)
+        v = vx.view()
+        fn = lambda: api.inclusive_scan(v, vo, stream=s)
+        if n < (1 << 24):
+            rows[name] = _row(_time(fn, s, 50, flush), n * 16, peak, l2="flushed between calls",
+                              l2_resident=_row(_time(fn, s, 200), n * 16, peak))
+        else:
+            rows[name] = _row(_time(fn, s, 20), n * 16, peak, l2="4 GiB per array > L2")
+        api.sync_status(s)
+        del vx, vo, v, x
+
+    # stencil: 16384^2 fp32, 8 row blocks of 2048 (+2 ghost rows), 100 steps
+    R = C = 16384
+    seg_rows = [2048] * 8
+    u0 = torch.from_numpy(inputs.uniform01_f32(inputs.SEED_STENCIL, R * C).reshape(R, C)).to(dev)
+    a = api.MdArray.from_tensor(u0, seg_rows)
+    b = api.MdArray.empty(seg_rows, C, dev)
+    t = api.MdArray.empty(seg_rows, C, dev)
+    ms = _time(lambda: api.stencil5(a, b, t, 100, stream=s), s, 3)
+    rows["stencil_16384^2_8blocks_100steps"] = _row(ms, 8 * R * C * 100, peak, ms_per_step=ms / 100,
+                                                    launches=101)
+    api.sync_status(s)
+
+    # autograd: stencil 50 steps, checkpoint every 10 (u0 gradient), fwd + bwd
+    blocks = [u0[2048 * k:2048 * (k + 1)].clone().requires_grad_(True) for k in range(8)]
+    gw = torch.ones(R, C, device=dev).split(2048)
+
+    def stencil_fb():
+        outs = AG.stencil(blocks, 50, 0.0, 0.25, checkpoint_every=10)
+        torch.autograd.backward(list(outs), list(gw))
+
+    ms = _time(stencil_fb, s, 2)
+    rows["autograd_stencil_16384^2_50steps_ckpt10_fwd+bwd"] = _row(
+        ms, 8 * R * C * 100, peak, note="100 stencil steps (50 fwd + 50 A^T); includes checkpoint copies")
+    del a, b, t, blocks, gw, u0
+
+    # autograd: scan n = 2^26 in 8 segments, fwd + bwd (reverse scan)
+    n = 1 << 26
+    xs = [q.clone().requires_grad_(True) for q in
+          torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_GRAD, n)).to(dev).split(n // 8)]
+    gy = list(torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_GRAD + 1, n)).to(dev).split(n // 8))
+
+    def scan_fb():
+        ys = AG.inclusive_scan(xs)
+        torch.autograd.backward(list(ys), gy)
+
+    ms = _time(scan_fb, s, 10)
+    rows["autograd_scan_2^26_8segs_fwd+bwd"] = _row(ms, 16 * n, peak)
+    del xs, gy
+
+    # batched: 4096 vectors, log-uniform [1e3, 1e6], 1-8 segments; one launch vs one per range
+    shapes = inputs.batch_shapes(inputs.SEED_BATCH, 4096)
+    tot = sum(map(sum, shapes))
+    X = api.packed_vectors(inputs.uniform_pm1_f32(inputs.SEED_BATCH_X, tot), shapes, device=dev)
+    P = api.packed_vectors(inputs.uniform_pm1_f32(inputs.SEED_BATCH_P, tot), shapes, device=dev)
+    Y = api.packed_vectors(None, shapes, device=dev)
+    dots = torch.zeros(len(shapes), dtype=torch.float32, device=dev)
+    batch = api.Batch(X, P, Y, dots)
+    # autotune on a calibration batch of the same distribution (other seeds), not the timed data
+    cshapes = inputs.batch_shapes(inputs.SEED_BATCH + 1, 4096)
+    ctot = sum(map(sum, cshapes))
+    CX = api.packed_vectors(inputs.uniform_pm1_f32(inputs.SEED_BATCH_X + 1, ctot), cshapes, device=dev)
+    CP = api.packed_vectors(inputs.uniform_pm1_f32(inputs.SEED_BATCH_P + 1, ctot), cshapes, device=dev)
+    CY = api.packed_vectors(None, cshapes, device=dev)
+    cal = api.Batch(CX, CP, CY, torch.zeros(len(cshapes), dtype=torch.float32, device=dev))
+    default_tune = batch.tune
+    chosen = cal.autotune(retune=True)
+    del cal, CX, CP, CY
+    ms_default = _time(lambda: batch.run(stream=s), s, 20)
+    batch.tune = chosen
+    ms_batch = _time(lambda: batch.run_graph(stream=s), s, 20)
+    ms_plain = _time(lambda: batch.run(stream=s), s, 20)
+    ms_per = _time(lambda: batch.run_per_range(stream=s), s, 3)
+    api.sync_status(s)
+    rows["batched_4096_vectors"] = _row(
+        ms_batch, 12 * tot, peak, elements=tot, tune=list(chosen), default_tune=list(default_tune),
+        ms_default_tune=ms_default, ms_one_launch_no_graph=ms_plain, ms_one_launch_per_range=ms_per,
+        speedup_vs_per_range=ms_per / ms_batch, launches=1, per_range_launches=2 * len(shapes))
+    return rows
 
 
 # ------------------------------------------------------------------------------------------
@@ -210,6 +328,8 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-rows", action="store_true", help="only the headline workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--log2n", type=int, default=28, help="headline size 2^log2n (profiling captures use less)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -219,6 +339,8 @@ def main() -> None:
     import torch
     from paper_2406_00158_gb300 import api, build
 
+    global N_ELEMS
+    N_ELEMS = 1 << args.log2n
     build.build()
     D = Dist("nccl")
     torch.cuda.set_device(D.local)
@@ -287,32 +409,34 @@ def main() -> None:
         traffic = json.load(open(tr_path)).get(dom)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    hx = torch.from_numpy(x).pin_memory()
-    hy = torch.from_numpy(y).pin_memory()
-    hout = torch.empty(N_ELEMS, dtype=torch.float32).pin_memory()
-    hdot = torch.empty(1, dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, min(10, K))
+    e2e_val = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(x).pin_memory()
+        hy = torch.from_numpy(y).pin_memory()
+        hout = torch.empty(N_ELEMS, dtype=torch.float32).pin_memory()
+        hdot = torch.empty(1, dtype=torch.float32).pin_memory()
+        e2e_steps = max(3, min(10, K))
 
-    def e2e_step():
-        vx.copy_from_host(hx, s)
-        vy.copy_from_host(hy, s)
-        step()
-        out.copy_to_host(hout, s)
-        hdot.copy_(dot, non_blocking=True)
+        def e2e_step():
+            vx.copy_from_host(hx, s)
+            vy.copy_from_host(hy, s)
+            step()
+            out.copy_to_host(hout, s)
+            hdot.copy_(dot, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    D.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(e2e_steps):
         e2e_step()
-    e1.record(s)
-    torch.cuda.synchronize()
-    e2e_ms = D.max(e0.elapsed_time(e1))
-    e2e_val = D.sum(bytes_step * e2e_steps) / (e2e_ms / 1e3) / 1e9
-    api.sync_status(s)
+        torch.cuda.synchronize()
+        D.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(e2e_steps):
+            e2e_step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        e2e_ms = D.max(e0.elapsed_time(e1))
+        e2e_val = D.sum(bytes_step * e2e_steps) / (e2e_ms / 1e3) / 1e9
+        api.sync_status(s)
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1)
     cpu = None
@@ -330,7 +454,8 @@ def main() -> None:
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": D.world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64, U[-1,1))",
-        "config": {"workload": WORKLOAD, "n": N_ELEMS, "segments": NSEG,
+        "config": {"workload": WORKLOAD if args.log2n == 28 else WORKLOAD.replace("2^28", f"2^{args.log2n}"),
+                   "n": N_ELEMS, "segments": NSEG,
                    "l2": "no flush: 3 GiB touched per step > 129 MB L2",
                    "parallelism": f"independent replicas x{D.world}" if D.world > 1 else "1 GPU"},
         "frac_of_peak": value / D.world / peak,
@@ -340,7 +465,7 @@ def main() -> None:
                                         "frac": v[1] / (v[0] / 1e3) / 1e9 / peak} for k, v in kern.items()}},
         "clocks": clk,
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 2 * N_ELEMS * 4,
-                "d2h_bytes_per_step": N_ELEMS * 4 + 4},
+                "d2h_bytes_per_step": N_ELEMS * 4 + 4} if e2e_val is not None else None,
         "gpu_launches": 2 * K,
         "cpu_baseline": cpu,
         "rows": rows,
