@@ -10,19 +10,23 @@
 //
 // Lookahead pipeline (persistent CTAs, tiles handed out by an atomic ticket).
 // Iteration k of a CTA handles two tiles:
-//   R phase, tile t_k: its loads were issued during iteration k-1 (so they
-//     overlap a whole iteration); fold the view, run the thread / warp / block
-//     scan tree and publish the tile aggregate.  The loads for t_{k+1} go out
-//     at once, the ticket for t_{k+2} is taken.
+//   R phase, tile t_k: its bytes were copied into a shared-memory stage by one
+//     TMA bulk copy (cp.async.bulk, completing on the stage's mbarrier) issued
+//     one iteration earlier; fold the view, run the thread / warp / block scan
+//     tree and publish the tile aggregate.  The freed stage is refilled with the
+//     next ticketed tile.
 //   S phase, tile t_{k-1}: warp 0 looks back over the predecessors (all of them
 //     published their aggregates at least an iteration ago, so the walk rarely
 //     waits), publishes the inclusive prefix, and the CTA re-reads the tile --
-//     from L2: the R-phase loads carry an evict_last policy, the re-read and the
-//     output stores evict_first -- scans it with the same tree plus the carry
-//     and stores it.
-// Waiting on a predecessor that is still loading stalls nothing but warp 0's
-// walk for a tile whose data arrived an iteration ago, which is what keeps
-// HBM busy; with one tile per CTA in flight the CTA idles during every walk.
+//     mostly an L2 hit: the re-read and the output stores carry an
+//     evict_first policy so they do not push the staged tiles out -- scans it
+//     with the same tree plus the carry and stores it.
+// Measured on GB300 (2^28 fp32): with one tile per CTA in flight a CTA spent
+// ~1.8 us loading and ~7 us waiting in lookback for predecessors still loading;
+// the lookahead order removes most of that wait, L2 eviction policies keep the
+// re-read in L2, and the shared-memory prefetch (two stages) frees the
+// registers that held the prefetched tile so that three CTAs fit per SM.  Deeper prefetch was slower: a tile ticketed long before it is
+// reduced publishes its aggregate late for its successors.
 //
 // Forward progress: a CTA consumes its tickets in increasing order, so the
 // smallest unfinished tile belongs to a CTA whose predecessors have all
@@ -39,8 +43,12 @@ constexpr int SCH = 8;            // 16-byte chunks per thread per tile (32 KB t
 constexpr int SNW = ST / 32;      // warps
 constexpr int SQ = SCH * SNW;     // warp-chunk totals per tile
 constexpr int SR = SQ / 32;       // totals per lane of warp 0
-constexpr int kLookbackG = 4;     // lookback slots per lane per round (128 tiles per round trip)
-constexpr int kMinBlocks = 2;     // resident CTAs per SM
+constexpr int kLookbackG = 1;     // lookback slots per lane per round (32 tiles per round trip)
+constexpr int kMinBlocks = 3;     // resident CTAs per SM
+constexpr int kStages = 2;        // shared-memory stages: the tile being reduced + the next
+constexpr int kTileBytes = ST * SCH * 16;
+
+constexpr int smem_bytes() { return kStages * kTileBytes; }
 static_assert(SQ % 32 == 0, "block-level scan assumes a multiple of 32 totals");
 
 template <typename T>
@@ -58,6 +66,17 @@ __device__ __forceinline__ int find_piece(const KPiece* pc, int n, int64_t tile)
   return lo;
 }
 
+// DR_CHECKED builds range- and alignment-check every address of the kernel; a
+// violation records DR_E_BOUNDS (with the check's id) in the status word and
+// the access is skipped instead of faulting.
+#ifndef DR_CHECKED
+#define DR_CHECKED 0
+#endif
+__device__ __forceinline__ bool chk(bool ok, unsigned id, unsigned* status) {
+  if (DR_CHECKED && !ok) raise_status(status, DR_E_BOUNDS, id);
+  return !DR_CHECKED || ok;
+}
+
 // Where a logical tile lives.
 struct TileRef {
   const KPiece* pc;
@@ -68,19 +87,26 @@ struct TileRef {
 template <typename T, bool REV>
 __device__ __forceinline__ TileRef tile_ref(const ScanParams& P, long long lt) {
   const int64_t pt = REV ? P.ntiles - 1 - lt : lt;
-  const KPiece* pc = &P.pc[find_piece(P.pc, P.npieces, pt)];
+  const int k = find_piece(P.pc, P.npieces, pt);
+  const KPiece* pc = &P.pc[k];
   const int64_t base = (pt - pc->tile_begin) * stile<T>();
-  return TileRef{pc, base, pc->vec_ok && pc->len - base >= stile<T>()};
+  const bool ok = chk(lt >= 0 && lt < P.ntiles && k >= 0 && k < P.npieces && base >= 0 && base < pc->len, 100,
+                      P.status);
+  return TileRef{pc, base, ok && pc->vec_ok && pc->len - base >= stile<T>()};
 }
 
 // 128-bit loads of a full tile (operand a, and b for a two-leaf view).
 template <typename T>
 __device__ __forceinline__ void load_full(const TileRef& r, bool two, int tid, unsigned long long pol,
-                                          V16<T> (&xa)[SCH], V16<T> (&xb)[SCH]) {
+                                          V16<T> (&xa)[SCH], V16<T> (&xb)[SCH], unsigned* status = nullptr) {
   constexpr int V = 16 / sizeof(T);
 #pragma unroll
-  for (int c = 0; c < SCH; ++c)
-    xa[c] = ld16_hint<T>(r.pc->a + (r.base + (int64_t)(c * ST + tid) * V) * (int64_t)sizeof(T), pol);
+  for (int c = 0; c < SCH; ++c) {
+    const int64_t e0 = r.base + (int64_t)(c * ST + tid) * V;
+    const char* src = r.pc->a + e0 * (int64_t)sizeof(T);
+    if (chk(e0 >= 0 && e0 + V <= r.pc->len && ((uintptr_t)src & 15) == 0, 104, status))
+      xa[c] = ld16_hint<T>(src, pol);
+  }
   if (two) {
 #pragma unroll
     for (int c = 0; c < SCH; ++c)
@@ -170,6 +196,24 @@ __device__ __forceinline__ T block_totals(const T* s_tot, int lane, T (&loc)[SR]
   return __shfl_sync(0xffffffffu, inc, 31);
 }
 
+// Thread 0: starts the load of tile `lt` into stage `st` (one bulk copy of a full
+// tile, completing on the stage's mbarrier), or completes the barrier's phase
+// without a copy (ragged tile, or no tile).  One arrival per call either way, so
+// a stage's barrier phase counts its uses.
+template <typename T, bool REV>
+__device__ __forceinline__ void stage_issue(const ScanParams& P, long long lt, char* stage,
+                                            unsigned long long* bar) {
+  if (lt < P.ntiles) {
+    const TileRef r = tile_ref<T, REV>(P, lt);
+    if (r.full) {
+      mbar_expect_tx(bar, kTileBytes);
+      bulk_g2s(stage, r.pc->a + r.base * (int64_t)sizeof(T), kTileBytes, bar);
+      return;
+    }
+  }
+  mbar_arrive(bar);
+}
+
 // KIND: 0 = one leaf, no ops (PLUS only); 2 = generic fused view.
 // REV: scan from the last element to the first (reverse inclusive scan).
 // EXCL: exclusive scan with init.
@@ -177,8 +221,10 @@ template <typename T, int OP, int KIND, bool REV, bool EXCL>
 __global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
   constexpr int V = 16 / sizeof(T);
   using O = Op<OP>;
+  extern __shared__ __align__(128) char s_stage[];  // kStages x kTileBytes
+  __shared__ __align__(8) unsigned long long s_bar[kStages];
   __shared__ T s_totR[SQ], s_totS[SQ], s_off[SQ];
-  __shared__ long long s_t;
+  __shared__ long long s_tk[kStages + 1];
   __shared__ T s_agg;
 
   WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
@@ -192,45 +238,62 @@ __global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T ident = O::template identity<T>();
   const unsigned long long keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
+  (void)keep;
 
-  // prologue: first tile and its loads, ticket of the second
-  if (tid == 0) s_t = (long long)atomicAdd(&hdr->ticket, 1ull);
-  __syncthreads();
-  long long t = s_t, tprev = -1;
-  __syncthreads();
-  if (tid == 0 && t < P.ntiles) s_t = (long long)atomicAdd(&hdr->ticket, 1ull);
-  V16<T> ra[SCH], rb[SCH];
-  if (t < P.ntiles) {
-    const TileRef r = tile_ref<T, REV>(P, t);
-    if (r.full) load_full<T>(r, two, tid, keep, ra, rb);
+  // prologue: tickets of the first kStages tiles (in order) and their loads
+  if (tid == 0) {
+    for (int d = 0; d < kStages; ++d) mbar_init(&s_bar[d], 1);
+    fence_mbar_init();
+    for (int d = 0; d < kStages; ++d) {
+      s_tk[d] = (long long)atomicAdd(&hdr->ticket, 1ull);
+      stage_issue<T, REV>(P, s_tk[d], s_stage + d * kTileBytes, &s_bar[d]);
+    }
   }
   __syncthreads();
-  long long tnext = t < P.ntiles ? s_t : t;
+  long long tk[kStages];  // tickets of the staged tiles, oldest first
+#pragma unroll
+  for (int d = 0; d < kStages; ++d) tk[d] = s_tk[d];
+  unsigned parity = 0;    // bit d: phase parity of stage d's next completion
+  long long tprev = -1;
   T aggprev = ident;  // warp 0: aggregate of tprev
+  int sidx = 0;       // stage of tk[0]
 
-  while (t < P.ntiles || tprev >= 0) {
+  while (tk[0] < P.ntiles || tprev >= 0) {
+    const long long t = tk[0];
     const bool haveR = t < P.ntiles, haveS = tprev >= 0;
-    const TileRef rs = haveS ? tile_ref<T, REV>(P, tprev) : TileRef{nullptr, 0, false};
 
-    // S-phase loads (L2 hits) go out first
-    V16<T> sa[SCH], sb[SCH];
-    if (haveS && rs.full) load_full<T>(rs, two, tid, drop, sa, sb);
-
-    // ---- R phase: aggregate of tile t
+    // ---- R phase: aggregate of tile t (from its stage; ragged tiles load directly)
     if (haveR) {
       const TileRef rr = tile_ref<T, REV>(P, t);
       T x[SCH][V], wx[SCH];
-      tile_values<T, KIND>(rr, two, tid, ve, ident, ra, rb, x);
+      if (rr.full) {
+        mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, P.spin_limit, P.status);
+        const char* st = s_stage + sidx * kTileBytes;
+#pragma unroll
+        for (int c = 0; c < SCH; ++c) {
+          V16<T> va;
+          const char* sp = st + (c * ST + tid) * 16;
+          if (chk(sidx >= 0 && sidx < kStages && ((uintptr_t)sp & 15) == 0, 103, P.status))
+            va = *reinterpret_cast<const V16<T>*>(sp);
+          V16<T> vb;
+          if (two) vb = ld16_hint<T>(rr.pc->b + (rr.base + (int64_t)(c * ST + tid) * V) * (int64_t)sizeof(T), keep);
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            if constexpr (KIND == 0) x[c][e] = va.v[e];
+            else x[c][e] = ve(va.v[e], two ? vb.v[e] : T(0));
+          }
+        }
+      } else {
+        V16<T> na[SCH], nb[SCH];
+        tile_values<T, KIND>(rr, two, tid, ve, ident, na, nb, x);
+      }
       local_scan<T, OP, REV>(x, wx, s_totR, lane, warp, ident);
     }
+    // the ticket after the staged ones (needed only at the end of the iteration)
+    const long long tlast = tk[kStages - 1];
+    long long tnew = P.ntiles;
+    if (tid == 0 && tlast < P.ntiles) tnew = (long long)atomicAdd(&hdr->ticket, 1ull);
     __syncthreads();
-    // the next tile's loads overlap this whole iteration; take the ticket after it
-    if (tnext < P.ntiles) {
-      const TileRef rn = tile_ref<T, REV>(P, tnext);
-      if (rn.full) load_full<T>(rn, two, tid, keep, ra, rb);
-    }
-    long long tnn = tnext;
-    if (tid == 0 && tnext < P.ntiles) tnn = (long long)atomicAdd(&hdr->ticket, 1ull);
 
     T prefix = ident;
     if (warp == 0) {
@@ -247,8 +310,11 @@ __global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__
       }
     }
 
-    // ---- S phase: scan tile tprev with its carry and store it
+    // ---- S phase: re-read tile tprev (L2), scan it with its carry and store it
     if (haveS) {
+      const TileRef rs = tile_ref<T, REV>(P, tprev);
+      V16<T> sa[SCH], sb[SCH];
+      if (rs.full) load_full<T>(rs, two, tid, drop, sa, sb, P.status);
       T x[SCH][V], wexc[SCH];
       tile_values<T, KIND>(rs, two, tid, ve, ident, sa, sb, x);
       local_scan<T, OP, REV>(x, wexc, s_totS, lane, warp, ident);
@@ -285,7 +351,9 @@ __global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__
           V16<T> o;
 #pragma unroll
           for (int e = 0; e < V; ++e) o.v[e] = y[e];
-          st16_hint<T>(rs.pc->o + off * (int64_t)sizeof(T), o, drop);
+          char* dst = rs.pc->o + off * (int64_t)sizeof(T);
+          if (chk(off >= 0 && off + V <= rs.pc->len && ((uintptr_t)dst & 15) == 0, 105, P.status))
+            st16_hint<T>(dst, o, drop);
         } else {
 #pragma unroll
           for (int e = 0; e < V; ++e)
@@ -293,16 +361,26 @@ __global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__
         }
       }
     }
-    if (tid == 0) s_t = tnn;
-    __syncthreads();  // s_t, s_agg published; shared totals free
+    if (tid == 0) s_tk[kStages] = tnew;
+    __syncthreads();  // s_tk, s_agg published; shared totals free
+    // refill the stage read in this R phase with the next ticketed tile (all reads
+    // of it happened before the barriers above)
+    const long long tn = tlast < P.ntiles ? s_tk[kStages] : P.ntiles;
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      stage_issue<T, REV>(P, tn, s_stage + sidx * kTileBytes, &s_bar[sidx]);
+    }
+    parity ^= 1u << sidx;
     if (warp == 0) aggprev = s_agg;
     tprev = haveR ? t : -1;
-    t = tnext;
-    tnext = s_t;
+#pragma unroll
+    for (int d = 0; d < kStages - 1; ++d) tk[d] = tk[d + 1];
+    tk[kStages - 1] = tn;
+    sidx = (sidx + 1) % kStages;
     __syncthreads();
   }
 
-  // ---- exit: the last CTA restores the header for the next launch
+  // ---- exit (no copy is in flight: every staged ticket left is past the end): the last CTA restores the header for the next launch
   if (tid == 0) {
     __threadfence();
     if (atomicAdd(&hdr->done, 1u) == gridDim.x - 1) {
@@ -318,7 +396,9 @@ template <typename T, int OP, int KIND, bool REV, bool EXCL>
 cudaError_t go(const ScanParams& p, int grid, cudaStream_t s) {
   static int per_sm = 0;
   if (!per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<T, OP, KIND, REV, EXCL>, ST, 0);
+    cudaFuncSetAttribute(k_scan<T, OP, KIND, REV, EXCL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_bytes());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<T, OP, KIND, REV, EXCL>, ST, smem_bytes());
     if (per_sm <= 0) per_sm = 1;
   }
   if (grid <= 0) {
@@ -328,7 +408,7 @@ cudaError_t go(const ScanParams& p, int grid, cudaStream_t s) {
     grid = sms * per_sm;
   }
   if (p.ntiles < grid) grid = (int)(p.ntiles > 0 ? p.ntiles : 1);
-  k_scan<T, OP, KIND, REV, EXCL><<<grid, ST, 0, s>>>(p);
+  k_scan<T, OP, KIND, REV, EXCL><<<grid, ST, smem_bytes(), s>>>(p);
   return cudaGetLastError();
 }
 
