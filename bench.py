@@ -195,11 +195,12 @@ def run_reference(args) -> None:
 # ------------------------------------------------------------------------------------------
 # the other hot-path rows (each timed with CUDA events on the launching stream)
 # ------------------------------------------------------------------------------------------
-def _time(fn, s, reps, flush=None):
-    """Mean ms per call over `reps` calls, CUDA events on stream s (flush between calls
-    if given, outside the measured interval)."""
+def _time(fn, s, reps, flush=None, warmup=2):
+    """Mean ms per call over `reps` calls after `warmup` untimed calls, CUDA events on
+    stream s (flush between calls if given, outside the measured interval)."""
     import torch
-    fn()
+    for _ in range(warmup):
+        fn()
     torch.cuda.synchronize()
     tot = 0.0
     for _ in range(reps):
@@ -267,7 +268,8 @@ def measure_rows(api, dev, s, peak) -> dict:
         outs = AG.stencil(blocks, 50, 0.0, 0.25, checkpoint_every=10)
         torch.autograd.backward(list(outs), list(gw))
 
-    ms = _time(stencil_fb, s, 2)
+    torch.cuda.empty_cache()
+    ms = _time(stencil_fb, s, 3)
     rows["autograd_stencil_16384^2_50steps_ckpt10_fwd+bwd"] = _row(
         ms, 8 * R * C * 100, peak, note="100 stencil steps (50 fwd + 50 A^T); includes checkpoint copies")
     del a, b, t, blocks, gw, u0

@@ -290,27 +290,32 @@ struct Slots<T, true> {  // [flag:32 | value bits:32] in one 64-bit word
   }
 };
 
+// 8-byte values: two 64-bit words, each [flag:32 | one half of the value:32].
+// Each word is written and read single-copy atomically; a reader accepts the
+// pair only when both words carry the same flag (epoch and state): a state is
+// published once per epoch, so matching flags identify one publication (an
+// A -> P overwrite in flight shows as a mismatch and is polled again).  One L2
+// round trip per poll, as for 4-byte values, instead of an acquire load of the
+// flag followed by a dependent load of the value.
 template <typename T>
-struct Slots<T, false> {  // {flag, pad, aggregate, inclusive prefix}; flag released after the value
+struct Slots<T, false> {
   char* base;
   static __host__ __device__ size_t bytes(int64_t ntiles) { return (size_t)ntiles * kSlotBytes; }
   __device__ void bind(char* b, int64_t) { base = b; }
-  __device__ __forceinline__ unsigned* flag(int64_t i) const {
-    return reinterpret_cast<unsigned*>(base + i * kSlotBytes);
-  }
-  __device__ __forceinline__ unsigned long long* val(int64_t i, unsigned state) const {
-    return reinterpret_cast<unsigned long long*>(base + i * kSlotBytes + (state == kStateP ? 16 : 8));
+  __device__ __forceinline__ unsigned long long* word(int64_t i) const {
+    return reinterpret_cast<unsigned long long*>(base + i * kSlotBytes);
   }
   __device__ __forceinline__ void publish(int64_t i, unsigned tag, unsigned state, T v) {
-    st_relaxed_u64(val(i, state), to_bits(v));
-    st_release_u32(flag(i), tag | state);
+    const unsigned long long bits = to_bits(v), f = (unsigned long long)(tag | state) << 32;
+    st_relaxed_u64(word(i), f | (bits & 0xffffffffull));
+    st_relaxed_u64(word(i) + 1, f | (bits >> 32));
   }
   __device__ __forceinline__ unsigned poll(int64_t i, unsigned tag, T& v) const {
-    unsigned f = ld_acquire_u32(flag(i));
-    if ((f & ~3u) != tag) return 0;
-    const unsigned s = f & 3u;
-    v = from_bits<T>(ld_relaxed_u64(val(i, s)));
-    return s;
+    const unsigned long long w0 = ld_relaxed_u64(word(i)), w1 = ld_relaxed_u64(word(i) + 1);
+    const unsigned f0 = (unsigned)(w0 >> 32), f1 = (unsigned)(w1 >> 32);
+    if (f0 != f1 || (f0 & ~3u) != tag) return 0;
+    v = from_bits<T>((w0 & 0xffffffffull) | (w1 << 32));
+    return f0 & 3u;
   }
 };
 
