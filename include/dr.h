@@ -87,11 +87,14 @@ typedef struct dr_piece {
   int64_t off[2];
 } dr_piece;
 
-/* Launch shape of the batched kernel (chosen by the autotuner or the caller). */
+/* Launch shape of the batched kernel (chosen by the autotuner or the caller).
+ * variant 0: one tile per CTA in registers; threads 128, 256 or 512; items 8 or 16.
+ * variant 1: lookahead pipeline with TMA-staged x and p; threads 256; items 16 or 32. */
 typedef struct dr_tune {
-  int32_t threads;      /* threads per CTA: 128, 256 or 512 */
-  int32_t items;        /* elements per thread per tile: 8 or 16 (fp32) */
-  int32_t ctas_per_sm;  /* persistent CTAs per SM: 1..8 */
+  int32_t threads;      /* threads per CTA */
+  int32_t items;        /* elements per thread per tile (fp32) */
+  int32_t ctas_per_sm;  /* persistent CTAs per SM: 1..8 (capped by occupancy) */
+  int32_t variant;      /* kernel variant, see above */
 } dr_tune;
 
 /* ------------------------------------------------------------------------ */

@@ -32,7 +32,8 @@ class dr_piece(ctypes.Structure):
 
 
 class dr_tune(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_int32), ("items", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+    _fields_ = [("threads", ctypes.c_int32), ("items", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("variant", ctypes.c_int32)]
 
 
 class DRError(RuntimeError):

@@ -369,9 +369,10 @@ class Batch:
 
     @property
     def tune(self) -> tuple:
+        """(threads, items, ctas_per_sm, variant) of the batched kernel."""
         t = L.dr_tune()
         call("dr_batch_get_tune", self.handle, ctypes.byref(t))
-        return (t.threads, t.items, t.ctas_per_sm)
+        return (t.threads, t.items, t.ctas_per_sm, t.variant)
 
     @tune.setter
     def tune(self, value) -> None:
@@ -382,7 +383,7 @@ class Batch:
         t = L.dr_tune()
         call("dr_batch_autotune", self.handle, 1 if retune else 0,
              cache_path.encode() if cache_path else None, ctypes.byref(t))
-        return (t.threads, t.items, t.ctas_per_sm)
+        return (t.threads, t.items, t.ctas_per_sm, t.variant)
 
     def __del__(self):
         h = getattr(self, "handle", None)

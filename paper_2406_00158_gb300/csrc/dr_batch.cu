@@ -23,7 +23,7 @@ struct dr_batch {
   std::vector<BPiece> pieces;
   std::vector<int> vec_piece_begin;  // pieces of vector v: [begin[v], begin[v+1])
   float* dots = nullptr;
-  dr_tune tune{256, 16, 4};
+  dr_tune tune{256, 16, 3, 1};
   int sms = 1;
   int device = -1;
   int64_t ntiles = 0;
@@ -84,7 +84,8 @@ static int build_tiles(dr_batch* b) {
 }
 
 static bool tune_ok(const dr_tune* t) {
-  return t && batch_shape_supported(t->threads, t->items) && t->ctas_per_sm >= 1 && t->ctas_per_sm <= 8;
+  return t && batch_shape_supported(t->variant, t->threads, t->items) && t->ctas_per_sm >= 1 &&
+         t->ctas_per_sm <= 8;
 }
 
 extern "C" int dr_batch_plan(int nvec, const dr_vec* const* x, const dr_vec* const* p, dr_vec* const* y,
@@ -313,8 +314,8 @@ static bool cache_lookup(const char* path, const std::string& key, dr_tune* t) {
     if (k == std::string::npos) continue;
     dr_tune c{};
     const char* s = line.c_str() + k + pat.size();
-    if (std::sscanf(s, " {\"threads\": %d, \"items\": %d, \"ctas_per_sm\": %d", &c.threads, &c.items,
-                    &c.ctas_per_sm) == 3 &&
+    if (std::sscanf(s, " {\"threads\": %d, \"items\": %d, \"ctas_per_sm\": %d, \"variant\": %d", &c.threads,
+                    &c.items, &c.ctas_per_sm, &c.variant) == 4 &&
         tune_ok(&c)) {
       *t = c;
       return true;
@@ -335,8 +336,9 @@ static void cache_store(const char* path, const std::string& key, const dr_tune&
       }
   }
   char buf[640];
-  std::snprintf(buf, sizeof buf, "\"%s\": {\"threads\": %d, \"items\": %d, \"ctas_per_sm\": %d, \"us\": %.2f}",
-                key.c_str(), t.threads, t.items, t.ctas_per_sm, us);
+  std::snprintf(buf, sizeof buf,
+                "\"%s\": {\"threads\": %d, \"items\": %d, \"ctas_per_sm\": %d, \"variant\": %d, \"us\": %.2f}",
+                key.c_str(), t.threads, t.items, t.ctas_per_sm, t.variant, us);
   keep.push_back(buf);
   const std::string tmp = std::string(path) + ".tmp";
   {
@@ -366,12 +368,15 @@ extern "C" int dr_batch_autotune(dr_batch* b, int mode, const char* cache_path, 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best_us = 1e30;
-  const int shapes[][2] = {{128, 16}, {256, 8}, {256, 16}, {512, 8}, {512, 16}};
-  const int ctas[] = {1, 2, 4, 8};
+  // {variant, threads, items, max CTAs per SM}
+  const int shapes[][4] = {{0, 128, 16, 8}, {0, 256, 8, 8}, {0, 256, 16, 8}, {0, 512, 8, 4},
+                           {0, 512, 16, 4}, {1, 256, 16, 3}, {1, 256, 32, 1}};
+  const int ctas[] = {1, 2, 3, 4, 8};
   int rc = DR_OK;
   for (const auto& sh : shapes) {
     for (int k : ctas) {
-      dr_tune t{sh[0], sh[1], k};
+      if (k > sh[3]) continue;
+      dr_tune t{sh[1], sh[2], k, sh[0]};
       if ((rc = dr_batch_set_tune(b, &t))) break;
       for (int w = 0; w < 2; ++w) dr_batch_run(b, (dr_stream_t)s);
       std::vector<float> ms;

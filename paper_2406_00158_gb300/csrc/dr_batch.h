@@ -43,7 +43,7 @@ struct BatchParams {
   int64_t spin_limit;
 };
 
-bool batch_shape_supported(int threads, int items);
+bool batch_shape_supported(int variant, int threads, int items);
 size_t batch_ws_bytes(int64_t ntiles, int nvec);
 cudaError_t launch_batch(const BatchParams& p, const dr_tune& t, int sms, cudaStream_t s);
 

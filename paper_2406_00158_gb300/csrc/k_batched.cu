@@ -12,8 +12,8 @@
 //    vector* (the vector's first tile publishes its inclusive prefix directly);
 //  * dot: each tile writes its partial; the vector's last tile to finish
 //    (per-vector counter) combines the partials in tile order: deterministic.
-// Launch shape (threads per CTA, elements per thread, CTAs per SM) is a
-// template / launch parameter chosen by the autotuner.
+// Launch shape (kernel variant, threads per CTA, elements per thread, CTAs
+// per SM) is a template / launch parameter chosen by the autotuner.
 #include "dr_batch.h"
 #include "dr_device.cuh"
 
@@ -205,6 +205,325 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
   }
 }
 
+// ---------------------------------------------------------------------------
+// Variant 1: the lookahead pipeline of the single-range scan, per vector.
+// Iteration k of a persistent CTA:
+//   R phase, tile t_k: x and p arrive in a shared-memory stage by two TMA bulk
+//     copies issued an iteration earlier (full tiles; ragged ones load
+//     directly); the tile's dot partial is written and, if it is the last tile
+//     of its vector to finish, the vector's dot is folded; the scan tree of x
+//     runs and the tile aggregate is published (the vector's first tile
+//     publishes its inclusive prefix).
+//   S phase, tile t_{k-1}: warp 0 looks back within the vector, publishes the
+//     inclusive prefix, and the CTA re-reads x (an L2 hit), scans it with the
+//     carry and stores y.
+// 12 B / element: x and p read once from HBM, y written once.
+// ---------------------------------------------------------------------------
+constexpr int LT = 256;  // threads per CTA
+constexpr int LNW = LT / 32;
+
+template <int CH>
+struct LaGeom {
+  static constexpr int TILE = LT * CH * 4;       // elements per tile
+  static constexpr int XB = TILE * 4;            // bytes of x (and of p) per tile
+  static constexpr int STAGE = 2 * XB;           // x then p
+  static constexpr int SMEM = 2 * STAGE;         // two stages
+  static constexpr int SQ = CH * LNW;
+  static constexpr int SR = (SQ + 31) / 32;
+};
+
+struct LaTile {  // what the S phase needs of the previous tile
+  const float* x;
+  float* y;
+  int64_t off, len, first;
+  bool full;
+};
+
+template <int CH>
+__device__ __forceinline__ LaTile la_tile(const BatchParams& P, long long t) {
+  const BTile bt = P.tiles[t];
+  const BPiece pc = P.pieces[bt.piece];
+  const BVec bv = P.vecs[pc.vec];
+  return LaTile{pc.x, pc.y, bt.off, pc.len, bv.first_tile,
+                pc.vec_ok != 0 && pc.len - bt.off >= LaGeom<CH>::TILE};
+}
+
+template <int CH>
+__device__ __forceinline__ void la_issue(const BatchParams& P, long long t, char* stage, unsigned long long* bar) {
+  using G = LaGeom<CH>;
+  if (t < P.ntiles) {
+    const BTile bt = P.tiles[t];
+    const BPiece pc = P.pieces[bt.piece];
+    if (pc.vec_ok && pc.len - bt.off >= G::TILE) {
+      mbar_expect_tx(bar, G::STAGE);
+      bulk_g2s(stage, pc.x + bt.off, G::XB, bar);
+      bulk_g2s(stage + G::XB, pc.p + bt.off, G::XB, bar);
+      return;
+    }
+  }
+  mbar_arrive(bar);
+}
+
+template <int CH>
+__device__ __forceinline__ void la_local_scan(float (&x)[CH][4], float (&wexc)[CH], float* s_tot, int lane,
+                                              int warp) {
+  float tsum[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    x[c][1] = fadd(x[c][0], x[c][1]);
+    x[c][2] = fadd(x[c][1], x[c][2]);
+    x[c][3] = fadd(x[c][2], x[c][3]);
+    tsum[c] = x[c][3];
+  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const float wi = warp_inclusive<float, DR_PLUS, false>(tsum[c], lane);
+    float we = __shfl_up_sync(0xffffffffu, wi, 1);
+    if (lane == 0) we = 0.f;
+    wexc[c] = we;
+    const float wt = __shfl_sync(0xffffffffu, wi, 31);
+    if (lane == 0) s_tot[c * LNW + warp] = wt;
+  }
+}
+
+template <int CH>
+__device__ __forceinline__ float la_block_totals(const float* s_tot, int lane, float (&loc)[LaGeom<CH>::SR],
+                                                 float& exc) {
+  using G = LaGeom<CH>;
+  float lsum = 0.f;
+#pragma unroll
+  for (int r = 0; r < G::SR; ++r) {
+    const int q = lane * G::SR + r;
+    loc[r] = q < G::SQ ? s_tot[q] : 0.f;
+    lsum = r == 0 ? loc[0] : fadd(lsum, loc[r]);
+  }
+  const float inc = warp_inclusive<float, DR_PLUS, false>(lsum, lane);
+  exc = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) exc = 0.f;
+  return __shfl_sync(0xffffffffu, inc, 31);
+}
+
+template <int CH, int MINB>
+__global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ BatchParams P) {
+  using G = LaGeom<CH>;
+  using O = Op<DR_PLUS>;
+  extern __shared__ __align__(128) char s_stage[];  // 2 stages x (x tile | p tile)
+  __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ float s_totR[G::SR * 32], s_totS[G::SR * 32], s_off[G::SR * 32], s_dot[LNW];
+  __shared__ long long s_tk[3];
+  __shared__ float s_agg;
+  __shared__ int s_last;
+
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
+  unsigned* vcount = reinterpret_cast<unsigned*>(P.ws + sizeof(WsHeader));
+  char* slot_base = P.ws + sizeof(WsHeader) + ((size_t)P.nvec * 4 + 15) / 16 * 16;
+  Slots<float> slots;
+  slots.bind(slot_base, P.ntiles);
+  float* dotpart = reinterpret_cast<float*>(slot_base + Slots<float>::bytes(P.ntiles));
+  const unsigned tag = (ld_relaxed_u32(&hdr->epoch) & 0x3fffffffu) << 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned long long drop = l2_policy_evict_first();
+
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    fence_mbar_init();
+    for (int d = 0; d < 2; ++d) {
+      s_tk[d] = (long long)atomicAdd(&hdr->ticket, 1ull);
+      la_issue<CH>(P, s_tk[d], s_stage + d * G::STAGE, &s_bar[d]);
+    }
+  }
+  __syncthreads();
+  long long tk0 = s_tk[0], tk1 = s_tk[1], tprev = -1;
+  unsigned parity = 0;
+  int sidx = 0;
+  float aggprev = 0.f;  // warp 0
+  LaTile prev{nullptr, nullptr, 0, 0, 0, false};
+
+  while (tk0 < P.ntiles || tprev >= 0) {
+    const long long t = tk0;
+    const bool haveR = t < P.ntiles, haveS = tprev >= 0;
+    LaTile cur{nullptr, nullptr, 0, 0, 0, false};
+    int vec = 0, vtiles = 0;
+
+    // ---- R phase: dot partial and scan aggregate of tile t
+    if (haveR) {
+      const BTile bt = P.tiles[t];
+      const BPiece pc = P.pieces[bt.piece];
+      const BVec bv = P.vecs[pc.vec];
+      vec = pc.vec;
+      vtiles = bv.ntiles;
+      cur = LaTile{pc.x, pc.y, bt.off, pc.len, bv.first_tile, pc.vec_ok != 0 && pc.len - bt.off >= G::TILE};
+      float x[CH][4], pr[CH][4];
+      if (cur.full) {
+        mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, P.spin_limit, P.status);
+        const char* st = s_stage + sidx * G::STAGE;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const V16<float> a = *reinterpret_cast<const V16<float>*>(st + (c * LT + tid) * 16);
+          const V16<float> b = *reinterpret_cast<const V16<float>*>(st + G::XB + (c * LT + tid) * 16);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            x[c][e] = a.v[e];
+            pr[c][e] = b.v[e];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int64_t i = bt.off + (int64_t)(c * LT + tid) * 4 + e;
+            const bool in = i < pc.len;
+            x[c][e] = in ? __ldg(pc.x + i) : 0.f;
+            pr[c][e] = in ? __ldg(pc.p + i) : 0.f;
+          }
+      }
+      float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        d0 = __fmaf_rn(x[c][0], pr[c][0], d0);
+        d1 = __fmaf_rn(x[c][1], pr[c][1], d1);
+        d2 = __fmaf_rn(x[c][2], pr[c][2], d2);
+        d3 = __fmaf_rn(x[c][3], pr[c][3], d3);
+      }
+      const float dsum = warp_reduce<float, DR_PLUS>((d0 + d1) + (d2 + d3));
+      if (lane == 0) s_dot[warp] = dsum;
+      float wx[CH];
+      la_local_scan<CH>(x, wx, s_totR, lane, warp);
+    }
+    long long tnew = P.ntiles;
+    if (tid == 0 && tk1 < P.ntiles) tnew = (long long)atomicAdd(&hdr->ticket, 1ull);
+    __syncthreads();
+
+    float prefix = 0.f;
+    if (warp == 0) {
+      if (haveR) {
+        float loc[G::SR], exc;
+        const float agg = la_block_totals<CH>(s_totR, lane, loc, exc);
+        if (lane == 0) {
+          slots.publish(t, tag, t == cur.first ? kStateP : kStateA, agg);
+          s_agg = agg;
+          float dt = 0.f;
+#pragma unroll
+          for (int w = 0; w < LNW; ++w) dt += s_dot[w];
+          dotpart[t] = dt;
+          __threadfence();
+          s_last = atomicAdd(vcount + vec, 1u) == (unsigned)vtiles - 1;
+        }
+        __syncwarp();
+        if (__shfl_sync(0xffffffffu, lane == 0 ? s_last : 0, 0)) {
+          // the vector's last tile to finish folds the dot partials in tile order
+          __threadfence();
+          float acc = 0.f;
+          for (int64_t i = cur.first + lane; i < cur.first + vtiles; i += 32)
+            acc += __int_as_float((int)ld_relaxed_u32(reinterpret_cast<const unsigned*>(dotpart + i)));
+          acc = warp_reduce<float, DR_PLUS>(acc);
+          if (lane == 0) {
+            P.dots[vec] = acc;
+            vcount[vec] = 0;
+          }
+        }
+      }
+      if (haveS && tprev != prev.first) {
+        prefix = lookback<float, O, 1>(slots, tprev - 1, prev.first, tag, lane, P.spin_limit, P.status);
+        if (lane == 0) slots.publish(tprev, tag, kStateP, prefix + aggprev);
+      }
+    }
+
+    // ---- S phase: y of tile tprev
+    if (haveS) {
+      float x[CH][4], wexc[CH];
+      if (prev.full) {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const V16<float> a = ld16_hint<float>(prev.x + prev.off + (int64_t)(c * LT + tid) * 4, drop);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) x[c][e] = a.v[e];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int64_t i = prev.off + (int64_t)(c * LT + tid) * 4 + e;
+            x[c][e] = i < prev.len ? __ldg(prev.x + i) : 0.f;
+          }
+      }
+      la_local_scan<CH>(x, wexc, s_totS, lane, warp);
+      __syncthreads();
+      if (warp == 0) {
+        float loc[G::SR], exc;
+        la_block_totals<CH>(s_totS, lane, loc, exc);
+        float o = fadd(prefix, exc);
+#pragma unroll
+        for (int r = 0; r < G::SR; ++r) {
+          const int q = lane * G::SR + r;
+          if (q < G::SQ) s_off[q] = o;
+          o = fadd(o, loc[r]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const float pre = fadd(s_off[c * LNW + warp], wexc[c]);
+        const int64_t off = prev.off + (int64_t)(c * LT + tid) * 4;
+        if (prev.full) {
+          V16<float> q;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) q.v[e] = fadd(pre, x[c][e]);
+          st16_hint<float>(prev.y + off, q, drop);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (off + e < prev.len) prev.y[off + e] = fadd(pre, x[c][e]);
+        }
+      }
+    }
+    if (tid == 0) s_tk[2] = tnew;
+    __syncthreads();
+    const long long tn = tk1 < P.ntiles ? s_tk[2] : P.ntiles;
+    if (tid == 0) {
+      fence_proxy_async_smem();  // every read of stage sidx happened before the barriers above
+      la_issue<CH>(P, tn, s_stage + sidx * G::STAGE, &s_bar[sidx]);
+    }
+    parity ^= 1u << sidx;
+    if (warp == 0) aggprev = s_agg;
+    prev = cur;
+    tprev = haveR ? t : -1;
+    tk0 = tk1;
+    tk1 = tn;
+    sidx ^= 1;
+    __syncthreads();
+  }
+
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&hdr->done, 1u) == gridDim.x - 1) {
+      hdr->ticket = 0;
+      hdr->done = 0;
+      hdr->epoch = hdr->epoch + 1;
+      __threadfence();
+    }
+  }
+}
+
+template <int CH, int MINB>
+cudaError_t go_la(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s) {
+  using G = LaGeom<CH>;
+  static int per = 0;
+  if (!per) {
+    cudaFuncSetAttribute(k_batch_la<CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_la<CH, MINB>, LT, G::SMEM);
+    if (per < 1) per = 1;
+  }
+  const int k = ctas_per_sm < per ? ctas_per_sm : per;
+  int64_t grid = (int64_t)sms * (k > 0 ? k : 1);
+  if (grid > p.ntiles) grid = p.ntiles > 0 ? p.ntiles : 1;
+  k_batch_la<CH, MINB><<<(unsigned)grid, LT, G::SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <int THREADS, int CH>
 cudaError_t go(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s) {
   static int per = 0;
@@ -221,8 +540,9 @@ cudaError_t go(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s) {
 
 }  // namespace
 
-bool batch_shape_supported(int threads, int items) {
-  return (threads == 128 || threads == 256 || threads == 512) && (items == 8 || items == 16);
+bool batch_shape_supported(int variant, int threads, int items) {
+  if (variant == 1) return threads == LT && (items == 16 || items == 32);
+  return variant == 0 && (threads == 128 || threads == 256 || threads == 512) && (items == 8 || items == 16);
 }
 
 size_t batch_ws_bytes(int64_t ntiles, int nvec) {
@@ -233,6 +553,11 @@ size_t batch_ws_bytes(int64_t ntiles, int nvec) {
 cudaError_t launch_batch(const BatchParams& p, const dr_tune& t, int sms, cudaStream_t s) {
   if (p.ntiles <= 0) return cudaSuccess;
   const int ch = t.items / 4;
+  if (t.variant == 1) {
+    if (ch == 4) return go_la<4, 3>(p, t.ctas_per_sm, sms, s);
+    if (ch == 8) return go_la<8, 1>(p, t.ctas_per_sm, sms, s);
+    return cudaErrorInvalidValue;
+  }
   if (t.threads == 128 && ch == 2) return go<128, 2>(p, t.ctas_per_sm, sms, s);
   if (t.threads == 128 && ch == 4) return go<128, 4>(p, t.ctas_per_sm, sms, s);
   if (t.threads == 256 && ch == 2) return go<256, 2>(p, t.ctas_per_sm, sms, s);

@@ -54,7 +54,8 @@ def small_shapes():
     return shapes + inputs.batch_shapes(inputs.SEED_BATCH + 7, 40, lo=1e3, hi=2e5)
 
 
-@pytest.mark.parametrize("tune", [None, (128, 16, 4), (256, 8, 2), (512, 16, 1)])
+@pytest.mark.parametrize("tune", [None, (128, 16, 4, 0), (256, 8, 2, 0), (512, 16, 1, 0), (256, 16, 3, 1),
+                                  (256, 32, 1, 1), (256, 16, 1, 1)])
 def test_batch_small_vs_oracle_repeat_graph_per_range(api, tune):
     shapes = small_shapes()
     x, p, xs, ps, ys, dots = build(api, shapes)
@@ -101,11 +102,12 @@ def test_autotune_and_cache(api, tmp_path):
     b = api.Batch(xs, ps, ys, dots)
     cache = str(tmp_path / "tune.json")
     chosen = b.autotune(retune=True, cache_path=cache)
-    assert chosen[0] in (128, 256, 512) and chosen[1] in (8, 16) and 1 <= chosen[2] <= 8
+    assert chosen[3] in (0, 1) and chosen[0] in (128, 256, 512) and chosen[1] in (8, 16, 32)
+    assert 1 <= chosen[2] <= 8
     assert b.tune == chosen
     text = open(cache).read()
-    assert '"threads": %d' % chosen[0] in text
-    b.tune = (256, 8, 1)
+    assert '"threads": %d' % chosen[0] in text and '"variant": %d' % chosen[3] in text
+    b.tune = (256, 8, 1, 0)
     assert b.autotune(retune=False, cache_path=cache) == chosen  # served from the cache
     dots.fill_(float("nan"))
     b.run()
