@@ -224,7 +224,7 @@ def _row(ms, nbytes, peak, **kw):
 
 
 def measure_rows(api, dev, s, peak) -> dict:
-    """The other hot-path rows, each on its own workload (see DESIGN.md section 8)."""
+    """The other hot-path rows, each on its own workload."""
     import torch
     from paper_2406_00158_gb300 import autograd as AG
     rows = {}
@@ -256,8 +256,12 @@ def measure_rows(api, dev, s, peak) -> dict:
     b = api.MdArray.empty(seg_rows, C, dev)
     t = api.MdArray.empty(seg_rows, C, dev)
     ms = _time(lambda: api.stencil5(a, b, t, 100, stream=s), s, 3)
+    try:
+        st_traffic = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get("stencil")
+    except (OSError, ValueError):
+        st_traffic = None
     rows["stencil_16384^2_8blocks_100steps"] = _row(ms, 8 * R * C * 100, peak, ms_per_step=ms / 100,
-                                                    launches=101)
+                                                    launches=101, traffic_per_step=st_traffic)
     api.sync_status(s)
 
     # autograd: stencil 50 steps, checkpoint every 10 (u0 gradient), fwd + bwd
@@ -332,6 +336,8 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--log2n", type=int, default=28, help="headline size 2^log2n (profiling captures use less)")
+    ap.add_argument("--stencil-only", type=int, default=0, metavar="N",
+                    help="profiling helper: only run the stencil on an N x N grid (8 row blocks), 5 steps")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -344,6 +350,19 @@ def main() -> None:
     global N_ELEMS
     N_ELEMS = 1 << args.log2n
     build.build()
+    if args.stencil_only:
+        n = args.stencil_only
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        u0 = torch.from_numpy(inputs.uniform01_f32(inputs.SEED_STENCIL, n * n).reshape(n, n)).to(dev)
+        rows = [n // 8] * 8
+        a = api.MdArray.from_tensor(u0, rows)
+        b = api.MdArray.empty(rows, n, dev)
+        t = api.MdArray.empty(rows, n, dev)
+        s = torch.cuda.current_stream()
+        ms = _time(lambda: api.stencil5(a, b, t, 5, stream=s), s, 3) / 5
+        api.sync_status(s)
+        print(json.dumps({"stencil_n": n, "ms_per_step": ms, "GB/s": 8 * n * n / (ms / 1e3) / 1e9}))
+        return
     D = Dist("nccl")
     torch.cuda.set_device(D.local)
     dev = torch.device("cuda", D.local)

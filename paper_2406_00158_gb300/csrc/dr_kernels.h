@@ -133,8 +133,11 @@ struct HaloParams {
 int reduce_tile_elems(int dtype);
 int scan_tile_elems(int dtype);
 int scale_tile_elems();
+#ifndef DR_STENCIL_ROWS
+#define DR_STENCIL_ROWS 64
+#endif
 constexpr int kStencilThreads = 128;   // 4 columns per thread -> 512 columns per CTA
-constexpr int kStencilRowsPerCta = 64;
+constexpr int kStencilRowsPerCta = DR_STENCIL_ROWS;
 
 size_t reduce_ws_bytes(int grid);
 size_t scan_ws_bytes(int64_t ntiles, int dtype);

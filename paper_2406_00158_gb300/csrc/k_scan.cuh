@@ -38,13 +38,22 @@
 namespace dr {
 namespace kscan {
 
+#ifndef DR_SCAN_CHUNKS
+#define DR_SCAN_CHUNKS 8
+#endif
+#ifndef DR_SCAN_MINB
+#define DR_SCAN_MINB 3
+#endif
+#ifndef DR_SCAN_LOOKBACK_G
+#define DR_SCAN_LOOKBACK_G 1
+#endif
 constexpr int ST = 256;           // threads per CTA
-constexpr int SCH = 8;            // 16-byte chunks per thread per tile (32 KB tiles)
+constexpr int SCH = DR_SCAN_CHUNKS;  // 16-byte chunks per thread per tile (8: 32 KB tiles)
 constexpr int SNW = ST / 32;      // warps
 constexpr int SQ = SCH * SNW;     // warp-chunk totals per tile
 constexpr int SR = SQ / 32;       // totals per lane of warp 0
-constexpr int kLookbackG = 1;     // lookback slots per lane per round (32 tiles per round trip)
-constexpr int kMinBlocks = 3;     // resident CTAs per SM
+constexpr int kLookbackG = DR_SCAN_LOOKBACK_G;  // lookback slots per lane per round
+constexpr int kMinBlocks = DR_SCAN_MINB;        // resident CTAs per SM
 constexpr int kStages = 2;        // shared-memory stages: the tile being reduced + the next
 constexpr int kTileBytes = ST * SCH * 16;
 

@@ -12,7 +12,9 @@
 // West / east neighbours come from the adjacent lanes by warp shuffle; lanes 0
 // and 31 read the one missing column with a scalar load (an L1/L2 hit: the
 // neighbouring warp loads that line).  Rows are fetched G at a time so G
-// independent 16-byte loads per thread are in flight.  The epilogue also
+// independent 16-byte loads per thread are in flight.  Measured on GB300
+// (16384^2, 8 blocks): G = 4 with 8 resident CTAs per SM (58 registers) moves
+// 6.2 TB/s; G = 8 (>100 registers) 5.5 TB/s; 10 CTAs per SM 4.8 TB/s.  The epilogue also
 // writes a block's first / last own row into the neighbouring blocks' ghost
 // rows of the output, which is the halo exchange for the next step.
 //
@@ -25,7 +27,13 @@ namespace {
 
 constexpr int TX = kStencilThreads;
 constexpr int RB = kStencilRowsPerCta;
-constexpr int G = 8;  // rows fetched per group
+#ifndef DR_STENCIL_GROUP
+#define DR_STENCIL_GROUP 4
+#endif
+#ifndef DR_STENCIL_MINB
+#define DR_STENCIL_MINB 8  // resident CTAs per SM asked of the register allocator (<= 64 registers)
+#endif
+constexpr int G = DR_STENCIL_GROUP;  // rows fetched per group
 
 __device__ __forceinline__ int find_seg(const StencilParams& P, int64_t rb) {
   int lo = 0, hi = P.nseg - 1;
@@ -79,7 +87,7 @@ __device__ __forceinline__ float upd(float n, float s, float w, float e, float c
 // wc term) and <N(u_bar_t), u_{t-1}> (the wn term; N = neighbour sum, and
 // <u_bar, N u> = <N u_bar, u> because N is symmetric) into acc[0], acc[1].
 template <int VW, bool WGRAD>
-__global__ void __launch_bounds__(TX) k_stencil5(const __grid_constant__ StencilParams P) {
+__global__ void __launch_bounds__(TX, DR_STENCIL_MINB) k_stencil5(const __grid_constant__ StencilParams P) {
   const int s = find_seg(P, blockIdx.y);
   const StencilSeg& S = P.seg[s];
   const int64_t C = P.cols;
