@@ -54,6 +54,9 @@ _SIGS = {
     "oracle_stencil5_f64_at": (None, [_P, _I64, _I64, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       _P, _I64, _P]),
     "oracle_stencil5_T_f64": (None, [_P, _I64, _I64, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P]),
+    "oracle_stream_f32": (None, [ctypes.c_int, _I64, _P, _P, _P, ctypes.c_float]),
+    "oracle_stream_f64": (None, [ctypes.c_int, _I64, _P, _P, _P, ctypes.c_double]),
+    "oracle_black_scholes_f64": (None, [_I64, _P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
 }
 
 
@@ -257,3 +260,36 @@ def fd_gradient(loss, x, h: float = 2.0 ** -10) -> np.ndarray:
         flat[j] = old
         g[j] = (lp - lm) / (2.0 * h)
     return g.reshape(x.shape)
+
+
+# ---------------------------------------------------------------------------
+# for_each element functions (Sec. 4.3 "for_each"; Sec. 5 STREAM, Black-Scholes)
+# ---------------------------------------------------------------------------
+
+STREAM_FNS = {"copy": 0, "scale": 1, "add": 2, "triad": 3}
+
+
+def stream(fn: str, a, b, c, q: float = 0.0):
+    """One STREAM kernel over zip(a, b, c) in the arrays' dtype (fp32 or fp64),
+    one rounding per operation: copy c=a; scale b=q*c; add c=a+b; triad a=b+q*c.
+    Returns new arrays (a, b, c) with the written one updated."""
+    dt = np.asarray(a).dtype
+    assert dt in (np.float32, np.float64)
+    a, b, c = (np.array(v, dtype=dt, copy=True) for v in (a, b, c))
+    assert a.size == b.size == c.size
+    f = lib().oracle_stream_f32 if dt == np.float32 else lib().oracle_stream_f64
+    f(STREAM_FNS[fn], a.size, _p(a), _p(b), _p(c), float(q))
+    return a, b, c
+
+
+def black_scholes_f64(S, X, T, r: float, sigma: float, aux: bool = False):
+    """European call and put prices in FP64.  With aux=True also returns an
+    (n, 4) array of (phi(d1), phi(d2), d1, X e^{-rT}) for error bounds."""
+    S, X, T = (_c(v, np.float64) for v in (S, X, T))
+    assert S.size == X.size == T.size
+    call = np.empty_like(S)
+    put = np.empty_like(S)
+    ax = np.empty((S.size, 4), np.float64) if aux else None
+    lib().oracle_black_scholes_f64(S.size, _p(S), _p(X), _p(T), float(r), float(sigma), _p(call), _p(put),
+                                   _p(ax) if aux else None)
+    return (call, put, ax) if aux else (call, put)

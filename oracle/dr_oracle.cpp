@@ -20,6 +20,8 @@
 //     inclusive scan) and the dot-product adjoint are written from their
 //     definitions; the stencil's transpose is written in scatter form so that
 //     the symmetry of the operator is checked, never assumed.
+//   * for_each's element functions (the STREAM kernels, Black-Scholes pricing)
+//     are written from their textbook definitions.
 //
 // Build: g++ -O2 -std=c++17 -fPIC -shared -ffp-contract=off (no fast-math).
 #include <algorithm>
@@ -269,6 +271,72 @@ void oracle_stencil5_T_f64(const double* v0, int64_t R, int64_t C, int steps, do
     std::swap(a, b);
   }
   std::memcpy(out, a.data(), sizeof(double) * R * C);
+}
+
+// --------------------------------------------------------------------------
+// for_each over a zip of k vectors with an element function (Sec. 4.3
+// "for_each"; Sec. 5's STREAM and Black-Scholes benchmarks).
+//
+// STREAM (McCalpin's four kernels), over zip(a, b, c) in the element type with
+// one IEEE rounding per operation -- the plain definition (no FMA contraction):
+//   copy:  c_i = a_i          scale: b_i = q * c_i
+//   add:   c_i = a_i + b_i    triad: a_i = b_i + q * c_i
+// --------------------------------------------------------------------------
+}  // extern "C"
+
+template <typename T>
+static void stream_op(int fn, int64_t n, T* a, T* b, T* c, T q) {
+  for (int64_t i = 0; i < n; ++i) {
+    switch (fn) {
+      case 0: c[i] = a[i]; break;
+      case 1: b[i] = q * c[i]; break;
+      case 2: c[i] = a[i] + b[i]; break;
+      case 3: {
+        const T qc = q * c[i];
+        a[i] = b[i] + qc;
+        break;
+      }
+    }
+  }
+}
+
+extern "C" {
+
+void oracle_stream_f32(int fn, int64_t n, float* a, float* b, float* c, float q) {
+  stream_op<float>(fn, n, a, b, c, q);
+}
+void oracle_stream_f64(int fn, int64_t n, double* a, double* b, double* c, double q) {
+  stream_op<double>(fn, n, a, b, c, q);
+}
+
+// European option prices under the Black-Scholes-Merton model (F. Black and
+// M. Scholes, J. Political Economy 81(3), 1973; R. C. Merton, Bell J. Econ. 4(1),
+// 1973), for spot S, strike X, time to expiry T (years), risk-free rate r and
+// volatility sigma, in FP64:
+//   d1 = (ln(S/X) + (r + sigma^2/2) T) / (sigma sqrt(T)),   d2 = d1 - sigma sqrt(T)
+//   call = S N(d1) - X e^{-rT} N(d2),   put = X e^{-rT} N(-d2) - S N(-d1)
+// with N the standard normal CDF, N(x) = erfc(-x / sqrt(2)) / 2.
+// Also returns, per option, the first-order error scale of an fp32 evaluation:
+// phi(d1) and phi(d2) (the normal density), d1, and K = X e^{-rT}.
+static double norm_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+static double norm_pdf(double x) { return std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI); }
+
+void oracle_black_scholes_f64(int64_t n, const double* S, const double* X, const double* T, double r,
+                              double sigma, double* call, double* put, double* aux /* n x 4 or NULL */) {
+  for (int64_t i = 0; i < n; ++i) {
+    const double sqt = std::sqrt(T[i]);
+    const double d1 = (std::log(S[i] / X[i]) + (r + 0.5 * sigma * sigma) * T[i]) / (sigma * sqt);
+    const double d2 = d1 - sigma * sqt;
+    const double K = X[i] * std::exp(-r * T[i]);
+    call[i] = S[i] * norm_cdf(d1) - K * norm_cdf(d2);
+    put[i] = K * norm_cdf(-d2) - S[i] * norm_cdf(-d1);
+    if (aux) {
+      aux[4 * i + 0] = norm_pdf(d1);
+      aux[4 * i + 1] = norm_pdf(d2);
+      aux[4 * i + 2] = d1;
+      aux[4 * i + 3] = K;
+    }
+  }
 }
 
 }  // extern "C"

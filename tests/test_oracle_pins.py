@@ -4,6 +4,7 @@ adjoint identities.  Each test is chosen so that a plausible slip in the oracle
 (a dropped term, an off-by-one, a wrong sign or transposed index, a wrong
 boundary) fails it.  CPU only."""
 import itertools
+import os
 import math
 from fractions import Fraction
 
@@ -378,3 +379,116 @@ def test_batch_shapes_recipe():
         assert 1 <= len(s) <= 8 and all(v > 0 for v in s)
         assert 1000 <= sum(s) <= 1_000_000
     assert shapes == inputs.batch_shapes(2411, 256)
+
+
+# ----------------------------------------------------------------------------------
+# for_each element functions: STREAM (one rounding per operation, element type)
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_stream_roles_and_closed_forms(dt):
+    n = 1000
+    i = np.arange(n, dtype=dt)
+    ones = np.ones(n, dt)
+    # copy: c = a, a and b untouched
+    a, b, c = oracle.stream("copy", i, 2 * i, ones)
+    assert np.array_equal(c, i) and np.array_equal(a, i) and np.array_equal(b, 2 * i)
+    # scale: b = q c (q = 3, integer-valued: exact); a, c untouched
+    a, b, c = oracle.stream("scale", ones, ones, i, 3.0)
+    assert np.array_equal(b, 3 * i) and np.array_equal(c, i) and np.array_equal(a, ones)
+    # add: c = a + b
+    a, b, c = oracle.stream("add", i, 7 * ones, ones)
+    assert np.array_equal(c, i + 7) and np.array_equal(b, 7 * ones)
+    # triad: a = b + q c with b = i, c = 1, q = 3 -> i + 3 (not 1 + 3 i: catches b <-> c)
+    a, b, c = oracle.stream("triad", 5 * ones, i, ones, 3.0)
+    assert np.array_equal(a, i + 3) and np.array_equal(b, i) and np.array_equal(c, ones)
+
+
+@pytest.mark.parametrize("dt,eps", [(np.float32, 2.0 ** -23), (np.float64, 2.0 ** -52)])
+def test_stream_triad_rounds_twice(dt, eps):
+    # q = c = 1 + eps: q*c = 1 + 2 eps + eps^2, rounded to 1 + 2 eps before the add;
+    # b = -1 leaves exactly 2 eps.  A fused multiply-add would keep eps^2 as well.
+    q = 1 + eps
+    a, _, _ = oracle.stream("triad", np.zeros(1, dt), -np.ones(1, dt), np.full(1, q, dt), q)
+    assert a[0] == dt(2 * eps)
+
+
+def test_stream_random_matches_numpy_definition():
+    # the definition in numpy's own (separately rounded) element ops
+    x = inputs.uniform_pm1_f32(RNG_KEY, 4096)
+    y = inputs.uniform_pm1_f32(RNG_KEY + 1, 4096)
+    z = inputs.uniform_pm1_f32(RNG_KEY + 2, 4096)
+    q = np.float32(0.4)
+    a, _, _ = oracle.stream("triad", x, y, z, float(q))
+    assert np.array_equal(a, y + q * z)
+    _, _, c = oracle.stream("add", x, y, z)
+    assert np.array_equal(c, x + y)
+
+
+# ----------------------------------------------------------------------------------
+# Black-Scholes-Merton European call / put (FP64)
+# ----------------------------------------------------------------------------------
+
+def _golden_bs():
+    path = os.path.join(os.path.dirname(__file__), "golden", "black_scholes_textbook.txt")
+    rows = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        rows.append({k: float(v) for k, v in (f.split("=") for f in line.split())})
+    return rows
+
+
+def test_black_scholes_textbook_example():
+    for g in _golden_bs():
+        call, put, aux = oracle.black_scholes_f64([g["S"]], [g["X"]], [g["T"]], g["r"], g["sigma"], aux=True)
+        d1 = aux[0, 2]
+        d2 = d1 - g["sigma"] * math.sqrt(g["T"])
+        dd, pd = int(g["d_decimals"]), int(g["price_decimals"])
+        assert round(d1, dd) == pytest.approx(g["d1"], abs=1e-12)
+        assert round(d2, dd) == pytest.approx(g["d2"], abs=1e-12)
+        assert round(call[0], pd) == pytest.approx(g["call"], abs=1e-12)
+        assert round(put[0], pd) == pytest.approx(g["put"], abs=1e-12)
+
+
+def _bs_inputs(n, key=RNG_KEY):
+    S = 5 + 25 * inputs.uniform01_f64(key, n)
+    X = 1 + 99 * inputs.uniform01_f64(key + 1, n)
+    T = 0.25 + 9.75 * inputs.uniform01_f64(key + 2, n)
+    return S, X, T
+
+
+def test_black_scholes_put_call_parity():
+    # call - put = S - X e^{-rT} for every option (a model-free identity): catches a
+    # sign or argument slip in either price
+    S, X, T = _bs_inputs(10000)
+    r, sigma = 0.02, 0.30
+    call, put = oracle.black_scholes_f64(S, X, T, r, sigma)
+    rhs = S - X * np.exp(-r * T)
+    assert np.max(np.abs((call - put) - rhs) / (S + X)) < 1e-14
+    assert np.all(call >= np.maximum(rhs, 0) - 1e-12 * (S + X))   # no-arbitrage lower bounds
+    assert np.all(put >= np.maximum(-rhs, 0) - 1e-12 * (S + X))
+    assert np.all(call <= S) and np.all(put <= X * np.exp(-r * T) + 1e-12)
+
+
+def test_black_scholes_at_the_money_forward_closed_form():
+    # S = X e^{-rT}: d1 = sigma sqrt(T)/2, d2 = -d1, so call = put = S erf(sigma sqrt(T) / (2 sqrt 2));
+    # depends on the sigma^2/2 drift term and on N's definition
+    for sigma, T, r, X in [(0.2, 1.0, 0.05, 100.0), (0.5, 2.0, 0.01, 30.0), (0.1, 0.25, 0.0, 7.0)]:
+        S = X * math.exp(-r * T)
+        call, put = oracle.black_scholes_f64([S], [X], [T], r, sigma)
+        want = S * math.erf(sigma * math.sqrt(T) / (2 * math.sqrt(2)))
+        assert call[0] == pytest.approx(want, rel=1e-13)
+        assert put[0] == pytest.approx(want, rel=1e-13)
+
+
+def test_black_scholes_zero_volatility_limit():
+    # sigma -> 0: the option is worth its discounted intrinsic value (r > 0 drift in d1)
+    S, X, T = _bs_inputs(2000, key=RNG_KEY + 7)
+    r = 0.05
+    keep = np.abs(np.log(S / X) + r * T) > 1e-3
+    S, X, T = S[keep], X[keep], T[keep]
+    call, put = oracle.black_scholes_f64(S, X, T, r, 1e-9)
+    K = X * np.exp(-r * T)
+    assert np.allclose(call, np.maximum(S - K, 0), rtol=0, atol=1e-9)
+    assert np.allclose(put, np.maximum(K - S, 0), rtol=0, atol=1e-9)
