@@ -278,6 +278,33 @@ def measure_rows(api, dev, s, peak) -> dict:
         ms, 8 * R * C * 100, peak, note="100 stencil steps (50 fwd + 50 A^T); includes checkpoint copies")
     del a, b, t, blocks, gw, u0
 
+    # for_each over k-ary zips: STREAM (fp64, 2^28 per array, 8 segments) and
+    # Black-Scholes (fp32, 2^28 options, 8 segments).  Arrays > L2: no flush needed.
+    n = 1 << 28
+    lens = [n // 8] * 8
+    sa, sb, sc = (api.SegmentedVector.from_tensor(torch.from_numpy(v).to(dev), lens)
+                  for v in inputs.stream_inputs(n, np.float64))
+    stream_bytes = {"copy": 16, "scale": 16, "add": 24, "triad": 24}
+    zips = {"copy": api.View.zipn(sa, sc), "scale": api.View.zipn(sb, sc),
+            "add": api.View.zipn(sa, sb, sc), "triad": api.View.zipn(sa, sb, sc)}
+    for fn, z in zips.items():
+        args = (3.0,) if fn in ("scale", "triad") else ()
+        ms = _time(lambda: api.for_each(z, fn, *args, stream=s), s, 20)
+        rows[f"stream_{fn}_f64_2^28_8segs"] = _row(ms, stream_bytes[fn] * n, peak,
+                                                   note="STREAM byte counting (no write-allocate)")
+    api.sync_status(s)
+    del zips, sa, sb, sc
+    S, X, Tm = inputs.black_scholes_inputs(n)
+    bs = [api.SegmentedVector.from_tensor(torch.from_numpy(v).to(dev), lens) for v in (S, X, Tm)]
+    bs += [api.SegmentedVector.empty(lens, torch.float32, dev) for _ in range(2)]
+    zbs = api.View.zipn(*bs)
+    r32, sig32 = float(np.float32(inputs.BS_R)), float(np.float32(inputs.BS_SIGMA))
+    ms = _time(lambda: api.for_each(zbs, "black_scholes", r32, sig32, stream=s), s, 20)
+    api.sync_status(s)
+    rows["black_scholes_f32_2^28_8segs"] = _row(ms, 20 * n, peak, options_per_s=n / (ms / 1e3),
+                                                note="S, X, T read; call, put written: 20 B/option")
+    del zbs, bs, S, X, Tm
+
     # autograd: scan n = 2^26 in 8 segments, fwd + bwd (reverse scan)
     n = 1 << 26
     xs = [q.clone().requires_grad_(True) for q in

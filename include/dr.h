@@ -194,6 +194,16 @@ int dr_view_zip(const dr_view* a, const dr_view* b, dr_view** out);
  * DR_MUL for the dot product of Algorithm 1. */
 int dr_view_zip_transform(const dr_view* zip, int op, dr_view** out);
 
+/* k-ary zip (Sec. 4.4 "Zip" over k ranges; 2 <= k <= DR_MAX_ZIP) of
+ * untransformed views (dr_view_of, possibly trimmed by take / drop) of one
+ * dtype: element i is the k-tuple of the operands' i-th elements, length the
+ * shortest operand's; the segments are re-cut at the union of all operands'
+ * boundaries.  Its elements are references: dr_for_each writes through them.
+ * `leaves` is a host array of k views; the zip refers to their vectors, not to
+ * the leaf handles, which may be destroyed afterwards. */
+#define DR_MAX_ZIP 6
+int dr_view_zipn(int k, const dr_view* const* leaves, dr_view** out);
+
 /* take / drop (Sec. 4.4 "Take and Drop"): the first l elements, or all but the
  * first f, via trimmed segments.  l and f are clamped to [0, size]. */
 int dr_view_take(const dr_view* base, int64_t l, dr_view** out);
@@ -201,8 +211,9 @@ int dr_view_drop(const dr_view* base, int64_t f, dr_view** out);
 
 int dr_view_destroy(dr_view* v);
 
-/* Queries (host only): size, arity (1 for single-valued, 2 for a raw zip),
- * element type, number of pieces of the (re-)segmentation, and the pieces. */
+/* Queries (host only): size, arity (1 for single-valued, k for a raw k-ary
+ * zip), element type, number of pieces of the (re-)segmentation, and the
+ * pieces (dr_piece reports the first two operands of a zip). */
 int dr_view_info(const dr_view* v, int64_t* size, int* arity, int* dtype, int* npieces);
 int dr_view_segments(const dr_view* v, int max_pieces, dr_piece* out);
 
@@ -238,6 +249,41 @@ int dr_reverse_inclusive_scan(const dr_view* in, dr_vec* out, dr_stream_t stream
  * for a given device).  Workspace as for dr_inclusive_scan. */
 int dr_transform_reduce(const dr_view* in, int op, const void* init, void* dev_result,
                         dr_stream_t stream);
+
+/* for_each (Sec. 4.3 "for_each") over a raw k-ary zip with a built-in element
+ * function; Sec. 5's STREAM and Black-Scholes benchmarks are for_each over a
+ * zip of their arrays.  The roles of the zip's operands, in order:
+ *   DR_FE_COPY          zip(a, c):           c = a
+ *   DR_FE_SCALE         zip(b, c):           b = q * c              args {q}
+ *   DR_FE_ADD           zip(a, b, c):        c = a + b
+ *   DR_FE_TRIAD         zip(a, b, c):        a = b + q * c          args {q}
+ *   DR_FE_BLACK_SCHOLES zip(S, X, T, C, P):  C, P = European call and put
+ *                       prices under the Black-Scholes-Merton model for spot S,
+ *                       strike X, expiry T (years)     args {r, sigma}
+ * dtype fp32 or fp64; args (nargs >= the function's count) are host doubles
+ * converted to the dtype.  STREAM functions round once per operation (no
+ * fused multiply-add), so results are bit-exact against a plain loop in the
+ * dtype; Black-Scholes calls CUDA's log, exp, sqrt and normcdf in the dtype.
+ * A written operand may be the very same elements as another operand
+ * (in place, e.g. zip(b, b) for b = q * b); any other overlap between a
+ * written operand and another operand is DR_E_INVAL.  One launch, no
+ * workspace, graph-capturable. */
+enum dr_foreach_fn {
+  DR_FE_COPY = 0,
+  DR_FE_SCALE = 1,
+  DR_FE_ADD = 2,
+  DR_FE_TRIAD = 3,
+  DR_FE_BLACK_SCHOLES = 4
+};
+int dr_for_each(const dr_view* zip, int fn, const double* args, int nargs, dr_stream_t stream);
+
+/* transform / copy of a view into a vector (Sec. 4.3: algorithms write their
+ * results through a range; Sec. 4.4: views are lazy until then):
+ * out_i = in_i for i < |in|, with in's fused transform / zip_transform chain
+ * evaluated in the load.  `out` has in's dtype and at least |in| elements; it
+ * may be the very storage of one of in's operands (in place); other overlap
+ * is DR_E_INVAL.  One launch, no workspace, graph-capturable. */
+int dr_transform(const dr_view* in, dr_vec* out, dr_stream_t stream);
 
 /* The dot product of dr_transform_reduce(zip(x, y) | DR_MUL, DR_PLUS) for callers
  * that cannot allocate device memory at the call (a framework that owns all device

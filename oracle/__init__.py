@@ -242,6 +242,27 @@ def zip_segments_bruteforce(lens_a, lens_b):
     return pieces
 
 
+def zip_segments_bruteforce_k(lens_list):
+    """k-ary form of zip_segments_bruteforce: the maximal runs of global indices
+    whose k owners (segment of each operand) stay the same.  Returns a list of
+    (segs, offs, length) with segs / offs k-tuples.  Small inputs only."""
+    owners = []
+    for lens in lens_list:
+        o = []
+        for k, L in enumerate(lens):
+            o.extend((k, j) for j in range(int(L)))
+        owners.append(o)
+    n = min(len(o) for o in owners)
+    pieces = []
+    for i in range(n):
+        segs = tuple(o[i][0] for o in owners)
+        if pieces and pieces[-1][0] == segs:
+            pieces[-1] = (segs, pieces[-1][1], pieces[-1][2] + 1)
+        else:
+            pieces.append((segs, tuple(o[i][1] for o in owners), 1))
+    return pieces
+
+
 # ---------------------------------------------------------------------------
 # central finite differences in FP64 (gradient checks)
 # ---------------------------------------------------------------------------

@@ -72,6 +72,7 @@ PROTOTYPES = {
     "dr_view_transform": (_I, [_P, _I, _D, _PP]),
     "dr_view_zip": (_I, [_P, _P, _PP]),
     "dr_view_zip_transform": (_I, [_P, _I, _PP]),
+    "dr_view_zipn": (_I, [_I, _PP, _PP]),
     "dr_view_take": (_I, [_P, _I64, _PP]),
     "dr_view_drop": (_I, [_P, _I64, _PP]),
     "dr_view_destroy": (_I, [_P]),
@@ -82,6 +83,8 @@ PROTOTYPES = {
     "dr_reverse_inclusive_scan": (_I, [_P, _P, _P]),
     "dr_transform_reduce": (_I, [_P, _I, _P, _P, _P]),
     "dr_scale_by_partner": (_I, [_P, _P, _P, _P, _P, _P]),
+    "dr_for_each": (_I, [_P, _I, ctypes.POINTER(_D), _I, _P]),
+    "dr_transform": (_I, [_P, _P, _P]),
     "dr_dot_f32_noalloc": (_I, [_I, _PI64, _PP, _PP, ctypes.c_float, _P, _P]),
     "dr_stencil5": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "dr_stencil5_T": (_I, [_P, _P, _P, _I, _D, _D, _P]),

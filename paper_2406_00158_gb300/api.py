@@ -190,6 +190,16 @@ class View:
         call("dr_view_zip", self.handle, other.handle, ctypes.byref(h))
         return View(h, [self, other])
 
+    @classmethod
+    def zipn(cls, *leaves) -> "View":
+        """k-ary zip (2 <= k <= 6) of untransformed views or vectors; for_each
+        writes through its elements."""
+        vs = [_as_view(v) for v in leaves]
+        arr = (ctypes.c_void_p * len(vs))(*[v.handle for v in vs])
+        h = _handle_out()
+        call("dr_view_zipn", len(vs), arr, ctypes.byref(h))
+        return cls(h, vs)
+
     def zip_transform(self, op) -> "View":
         h = _handle_out()
         call("dr_view_zip_transform", self.handle, _op(op), ctypes.byref(h))
@@ -262,6 +272,25 @@ def transform_reduce(inp, out: torch.Tensor, op="plus", init=0, stream=None) -> 
     init_c = _scalar_bytes(init, _DT[out.dtype])
     call("dr_transform_reduce", v.handle, _op(op), ctypes.byref(init_c), ctypes.c_void_p(out.data_ptr()),
          stream_handle(stream))
+    return out
+
+
+FOR_EACH_FNS = {"copy": 0, "scale": 1, "add": 2, "triad": 3, "black_scholes": 4}
+
+
+def for_each(zip_view: View, fn, *args: float, stream=None) -> None:
+    """for_each over a k-ary zip with a built-in element function (operand roles
+    in dr.h): copy zip(a, c); scale zip(b, c), q; add zip(a, b, c);
+    triad zip(a, b, c), q; black_scholes zip(S, X, T, C, P), r, sigma."""
+    code = FOR_EACH_FNS[fn] if isinstance(fn, str) else int(fn)
+    arr = (ctypes.c_double * max(1, len(args)))(*[float(a) for a in args])
+    call("dr_for_each", zip_view.handle, code, arr, len(args), stream_handle(stream))
+
+
+def transform(inp, out: SegmentedVector, stream=None) -> SegmentedVector:
+    """out_i = inp_i: a (fused) view written out to a vector."""
+    v = _as_view(inp)
+    call("dr_transform", v.handle, out.handle, stream_handle(stream))
     return out
 
 

@@ -117,7 +117,7 @@ void Workspace::release() {
 // re-segmentation (Sec. 4.4 "Zip")
 // ---------------------------------------------------------------------------
 std::vector<Piece> resegment(const std::vector<std::vector<Seg>>& ops, int esz) {
-  const size_t k = ops.size();
+  const size_t k = std::min<size_t>(ops.size(), kMaxZip);  // callers pass at most kMaxZip
   std::vector<Piece> out;
   std::vector<size_t> si(k, 0);
   std::vector<int64_t> used(k, 0);
@@ -424,8 +424,7 @@ static dr_view* clone_view(const dr_view* b) {
   w->dtype = b->dtype;
   w->arity = b->arity;
   w->nleaf = b->nleaf;
-  w->leaf[0] = b->leaf[0];
-  w->leaf[1] = b->leaf[1];
+  for (int l = 0; l < kMaxZip; ++l) w->leaf[l] = b->leaf[l];
   std::memcpy(w->npre, b->npre, sizeof w->npre);
   std::memcpy(w->pre_op, b->pre_op, sizeof w->pre_op);
   std::memcpy(w->pre_arg, b->pre_arg, sizeof w->pre_arg);
@@ -476,6 +475,29 @@ extern "C" int dr_view_zip(const dr_view* a, const dr_view* b, dr_view** out) {
     w->pre_op[1][k] = b->post_op[k];
     w->pre_arg[1][k] = b->post_arg[k];
   }
+  w->recompute();
+  *out = w;
+  return DR_OK;
+}
+
+extern "C" int dr_view_zipn(int k, const dr_view* const* leaves, dr_view** out) {
+  clear_error();
+  const char* who = "dr_view_zipn";
+  if (!leaves || !out) return fail(DR_E_INVAL, "%s: NULL argument", who);
+  if (k < 2 || k > kMaxZip) return fail(DR_E_UNSUPPORTED, "%s: k = %d outside [2, %d]", who, k, kMaxZip);
+  for (int l = 0; l < k; ++l) {
+    const dr_view* v = leaves[l];
+    if (!v) return fail(DR_E_INVAL, "%s: leaf %d is NULL", who, l);
+    if (v->arity != 1 || v->nleaf != 1 || v->npost != 0 || v->npre[0] != 0)
+      return fail(DR_E_UNSUPPORTED, "%s: leaf %d is not an untransformed view of one vector", who, l);
+    if (v->dtype != leaves[0]->dtype) return fail(DR_E_DTYPE, "%s: leaf dtypes differ", who);
+  }
+  dr_view* w = new (std::nothrow) dr_view();
+  if (!w) return fail(DR_E_NOMEM, "%s: out of host memory", who);
+  w->dtype = leaves[0]->dtype;
+  w->arity = k;
+  w->nleaf = k;
+  for (int l = 0; l < k; ++l) w->leaf[l] = leaves[l]->leaf[0];
   w->recompute();
   *out = w;
   return DR_OK;
@@ -584,6 +606,11 @@ static int call_pieces(const dr_view* in, const dr_vec* out, int tile, KPiece* p
   *npieces = (int)ps.size();
   *ntiles = t;
   return DR_OK;
+}
+
+// True when [p, p + n) and [q, q + n) overlap but do not coincide.
+static bool partial_overlap(const char* p, const char* q, int64_t nbytes) {
+  return p != q && p < q + nbytes && q < p + nbytes;
 }
 
 static int check_single(const dr_view* in, const char* who) {
@@ -698,6 +725,100 @@ extern "C" int dr_scale_by_partner(const dr_vec* x, const dr_vec* y, const float
   }
   p.ntiles = t;
   cudaError_t e = launch_scale(p, 0, (cudaStream_t)stream);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
+}
+
+// ---------------------------------------------------------------------------
+// for_each over a k-ary zip, and transform
+// ---------------------------------------------------------------------------
+namespace {
+struct FeSig {
+  int arity, nargs;
+  unsigned written;  // bit l: operand l is written
+};
+bool fe_sig(int fn, FeSig* s) {
+  switch (fn) {
+    case DR_FE_COPY: *s = {2, 0, 1u << 1}; return true;
+    case DR_FE_SCALE: *s = {2, 1, 1u << 0}; return true;
+    case DR_FE_ADD: *s = {3, 0, 1u << 2}; return true;
+    case DR_FE_TRIAD: *s = {3, 1, 1u << 0}; return true;
+    case DR_FE_BLACK_SCHOLES: *s = {5, 2, (1u << 3) | (1u << 4)}; return true;
+  }
+  return false;
+}
+}  // namespace
+
+extern "C" int dr_for_each(const dr_view* zip, int fn, const double* args, int nargs, dr_stream_t stream) {
+  clear_error();
+  const char* who = "dr_for_each";
+  if (!zip) return fail(DR_E_INVAL, "%s: NULL zip", who);
+  FeSig sig;
+  if (!fe_sig(fn, &sig)) return fail(DR_E_INVAL, "%s: unknown function %d", who, fn);
+  if (zip->arity != sig.arity || zip->nleaf != sig.arity)
+    return fail(DR_E_INVAL, "%s: function %d takes a zip of %d vectors (got arity %d)", who, fn, sig.arity,
+                zip->arity);
+  if (zip->dtype != DR_F32 && zip->dtype != DR_F64) return fail(DR_E_DTYPE, "%s: fp32 or fp64 only", who);
+  if (nargs < sig.nargs || (sig.nargs > 0 && !args))
+    return fail(DR_E_INVAL, "%s: function %d needs %d scalar arguments", who, fn, sig.nargs);
+  const int esz = esize(zip->dtype);
+  if ((int)zip->pieces.size() > kMaxPieces)
+    return fail(DR_E_UNSUPPORTED, "%s: %zu pieces after re-segmentation (limit %d)", who, zip->pieces.size(),
+                kMaxPieces);
+  static thread_local ForEachParams p;
+  std::memset(&p, 0, sizeof p);
+  p.fn = fn;
+  p.dtype = zip->dtype;
+  for (int a = 0; a < sig.nargs; ++a) p.arg[a] = args[a];
+  const int tile = foreach_tile_elems(zip->dtype);
+  int64_t t = 0;
+  int np = 0;
+  for (const Piece& q : zip->pieces) {
+    if (q.len == 0) continue;
+    for (int w = 0; w < sig.arity; ++w) {
+      if (!(sig.written >> w & 1)) continue;
+      for (int l = 0; l < sig.arity; ++l)
+        if (l != w && partial_overlap(q.p[w], q.p[l], q.len * esz))
+          return fail(DR_E_INVAL, "%s: written operand %d overlaps operand %d", who, w, l);
+    }
+    FePiece& k = p.pc[np++];
+    bool al = true;
+    for (int l = 0; l < sig.arity; ++l) {
+      k.p[l] = q.p[l];
+      al = al && (uintptr_t)q.p[l] % 16 == 0;
+    }
+    k.len = q.len;
+    k.tile_begin = t;
+    k.vec_ok = al;
+    t += (q.len + tile - 1) / tile;
+  }
+  p.npieces = np;
+  p.ntiles = t;
+  if (t == 0) return DR_OK;
+  cudaError_t e = launch_for_each(p, (cudaStream_t)stream);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
+}
+
+extern "C" int dr_transform(const dr_view* in, dr_vec* out, dr_stream_t stream) {
+  clear_error();
+  const char* who = "dr_transform";
+  if (int r = check_single(in, who)) return r;
+  if (!out) return fail(DR_E_INVAL, "%s: NULL output", who);
+  if (out->dtype != in->dtype) return fail(DR_E_DTYPE, "%s: output dtype differs from input", who);
+  if (out->n < in->size)
+    return fail(DR_E_INVAL, "%s: output has %lld elements, input %lld", who, (long long)out->n, (long long)in->size);
+  if (in->size == 0) return DR_OK;
+  static thread_local TransformParams p;
+  std::memset(&p, 0, sizeof p);
+  p.vc = in->code();
+  p.dtype = in->dtype;
+  if (int r = call_pieces(in, out, foreach_tile_elems(in->dtype), p.pc, &p.npieces, &p.ntiles)) return r;
+  const int esz = esize(in->dtype);
+  for (int i = 0; i < p.npieces; ++i) {
+    const KPiece& k = p.pc[i];
+    if (partial_overlap(k.o, k.a, k.len * esz) || (k.b && partial_overlap(k.o, k.b, k.len * esz)))
+      return fail(DR_E_INVAL, "%s: output overlaps an operand of the view", who);
+  }
+  cudaError_t e = launch_transform(p, (cudaStream_t)stream);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
 }
 

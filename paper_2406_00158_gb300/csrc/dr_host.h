@@ -45,12 +45,12 @@ struct Seg {
   int64_t off;  // element offset of p within that segment
 };
 
-// A piece of a k-way re-segmentation (k <= 4).
+// A piece of a k-way re-segmentation (k <= kMaxZip).
 struct Piece {
   int64_t start, len;
-  char* p[4];
-  int32_t seg[4];
-  int64_t off[4];
+  char* p[kMaxZip];
+  int32_t seg[kMaxZip];
+  int64_t off[kMaxZip];
 };
 
 // Cuts k segment lists at the union of their boundaries (Sec. 4.4 "Zip": take
@@ -84,9 +84,9 @@ struct dr_view {
     int64_t lo, hi;  // element window of the vector (take / drop)
   };
   int dtype = 0;
-  int arity = 1;  // 1 = single-valued, 2 = raw zip
+  int arity = 1;  // 1 = single-valued, k >= 2 = raw k-ary zip
   int nleaf = 1;
-  Leaf leaf[2];
+  Leaf leaf[dr::kMaxZip];
   int npre[2] = {0, 0};
   int pre_op[2][dr::kMaxChain];
   double pre_arg[2][dr::kMaxChain];

@@ -14,6 +14,7 @@ namespace dr {
 
 constexpr int kMaxChain = 4;     // unary ops per chain in a fused view
 constexpr int kMaxPieces = 128;  // segments (after re-segmentation) per single-range call
+constexpr int kMaxZip = DR_MAX_ZIP;  // operands of a k-ary zip (and of one re-segmentation)
 
 // Fused view: element = post(zipop(pre0(a), pre1(b))) (or post(pre0(a)) for one leaf).
 // kind: 0 = one leaf, no ops; 1 = two leaves times each other, no other ops
@@ -97,6 +98,34 @@ struct ScaleParams {  // dot adjoint: gx = g*y, gy = g*x
   } pc[kMaxPieces];
 };
 
+// for_each over a k-ary zip: piece i has `len` elements at p[0..k-1] (byte
+// pointers at the piece's first element).  vec_ok: every p is 16-byte aligned.
+struct FePiece {
+  char* p[kMaxZip];
+  int64_t len;
+  int64_t tile_begin;
+  int32_t vec_ok;
+  int32_t pad_;
+};
+
+struct ForEachParams {
+  int fn;      // enum dr_foreach_fn
+  int dtype;   // DR_F32 or DR_F64
+  int npieces;
+  int64_t ntiles;
+  double arg[2];
+  FePiece pc[kMaxPieces];
+};
+
+// transform: out = the fused view, piece by piece (KPiece a, b = leaves, o = out).
+struct TransformParams {
+  KViewCode vc;
+  int dtype;
+  int npieces;
+  int64_t ntiles;
+  KPiece pc[kMaxPieces];
+};
+
 struct StencilSeg {
   const float* in;   // allocation incl. ghost rows: (rows + 2) * cols
   const float* prev; // weight-gradient step only: the forward state u_{t-1} (same layout)
@@ -133,6 +162,7 @@ struct HaloParams {
 int reduce_tile_elems(int dtype);
 int scan_tile_elems(int dtype);
 int scale_tile_elems();
+int foreach_tile_elems(int dtype);  // for_each and transform
 #ifndef DR_STENCIL_ROWS
 #define DR_STENCIL_ROWS 64
 #endif
@@ -148,6 +178,8 @@ cudaError_t launch_scan(const ScanParams& p, bool reverse, int grid, cudaStream_
 cudaError_t launch_scale(const ScaleParams& p, int grid, cudaStream_t s);
 cudaError_t launch_stencil(const StencilParams& p, cudaStream_t s);
 cudaError_t launch_halo(const HaloParams& p, cudaStream_t s);
+cudaError_t launch_for_each(const ForEachParams& p, cudaStream_t s);
+cudaError_t launch_transform(const TransformParams& p, cudaStream_t s);
 
 // Resident-CTA count helpers (host).
 int reduce_grid(int dtype);

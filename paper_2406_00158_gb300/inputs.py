@@ -41,6 +41,17 @@ SEED_GRAD = 2410
 SEED_BATCH = 2411     # batch shapes
 SEED_BATCH_X = 3411   # batch values x
 SEED_BATCH_P = 4411   # batch partner values p
+SEED_STREAM = 2412    # STREAM arrays a, b, c: streams 2412, 2413, 2414
+SEED_BS = 2415        # Black-Scholes S, X, T: streams 2415, 2416, 2417
+
+# Black-Scholes option batch (the paper gives no sizes or ranges): spot S in
+# [5, 30), strike X in [1, 100), expiry T in [0.25, 10) years, fp32; rate and
+# volatility are scalars (r = 0.02, sigma = 0.30 rounded to fp32).
+BS_S_RANGE = (5.0, 30.0)
+BS_X_RANGE = (1.0, 100.0)
+BS_T_RANGE = (0.25, 10.0)
+BS_R = 0.02
+BS_SIGMA = 0.30
 
 
 def _mix64(z: np.ndarray) -> np.ndarray:
@@ -167,3 +178,20 @@ def batch_shapes(key: int, nvec: int, lo: float = 1e3, hi: float = 1e6, max_seg:
         s = 1 + ((int(r[1]) >> 32) * max_seg >> 32)
         shapes.append(random_cut_segments(vkey ^ 0x5EC5, L, s))
     return shapes
+
+
+def black_scholes_inputs(n: int, key: int = SEED_BS):
+    """fp32 arrays (S, X, T) of n options: lo + (hi - lo) * U[0, 1) per range,
+    evaluated in fp32."""
+    out = []
+    for j, (lo, hi) in enumerate((BS_S_RANGE, BS_X_RANGE, BS_T_RANGE)):
+        u = uniform01_f32(key + j, n)
+        out.append((np.float32(lo) + np.float32(hi - lo) * u).astype(np.float32))
+    return tuple(out)
+
+
+def stream_inputs(n: int, dtype=np.float64, key: int = SEED_STREAM):
+    """STREAM arrays (a, b, c), values in [-1, 1)."""
+    if dtype == np.float32:
+        return tuple(uniform_pm1_f32(key + j, n) for j in range(3))
+    return tuple(2.0 * uniform01_f64(key + j, n) - 1.0 for j in range(3))

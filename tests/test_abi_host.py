@@ -192,3 +192,107 @@ def test_status_knobs(lib):
     assert lib.dr_set_spin_limit(0) == L.DR_E_INVAL
     assert lib.dr_set_spin_limit(1 << 21) == 0
     assert lib.dr_debug_skip_publish(-5) == 0
+
+
+# ----------------------------------------------------------------------------------
+# k-ary zip, for_each and transform: host-side rules (no launch)
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("trial", range(12))
+def test_zipn_resegmentation_matches_oracle(lib, trial):
+    k = 2 + trial % 5
+    lens_list, views = [], []
+    for o in range(k):
+        n = 150 - (o * trial) % 9
+        lens = inputs.random_cut_segments(700 + 10 * trial + o, n, 1 + (trial + 2 * o) % 6)
+        if (trial + o) % 3 == 0:
+            lens = [0] + lens
+        _, h = make_vec(lens, ptrs=fake_ptrs(lens, base=(o + 1) << 36))
+        lens_list.append(lens)
+        views.append(view_of(h))
+    z = ctypes.c_void_p()
+    assert lib.dr_view_zipn(k, (ctypes.c_void_p * k)(*views), ctypes.byref(z)) == 0
+    size, got = pieces(z)
+    exp = oracle.zip_segments_bruteforce_k(lens_list)
+    assert size == min(sum(l) for l in lens_list)
+    # dr_piece reports the first two operands; the cuts of all k show in the lengths
+    assert got == [(s[0], f[0], s[1], f[1], n) for s, f, n in exp]
+    arity = ctypes.c_int()
+    lib.dr_view_info(z, None, ctypes.byref(arity), None, None)
+    assert arity.value == k
+
+
+def test_zipn_composition_rules(lib):
+    _, ha = make_vec([8])
+    _, hb = make_vec([8], ptrs=[1 << 41])
+    _, hd = make_vec([8], dtype=L.DR_F64, ptrs=[1 << 42])
+    va, vb, vd = view_of(ha), view_of(hb), view_of(hd)
+    z = ctypes.c_void_p()
+    arr = lambda *v: (ctypes.c_void_p * len(v))(*v)
+    assert lib.dr_view_zipn(1, arr(va), ctypes.byref(z)) == L.DR_E_UNSUPPORTED
+    assert lib.dr_view_zipn(7, arr(*([va] * 7)), ctypes.byref(z)) == L.DR_E_UNSUPPORTED
+    assert lib.dr_view_zipn(2, arr(va, vd), ctypes.byref(z)) == L.DR_E_DTYPE
+    assert lib.dr_view_zipn(2, arr(va, None), ctypes.byref(z)) == L.DR_E_INVAL
+    t = ctypes.c_void_p()
+    assert lib.dr_view_transform(va, L.DR_U_SCALE, 2.0, ctypes.byref(t)) == 0
+    assert lib.dr_view_zipn(2, arr(va, t), ctypes.byref(z)) == L.DR_E_UNSUPPORTED  # transformed leaf
+    z2 = ctypes.c_void_p()
+    assert lib.dr_view_zipn(2, arr(va, vb), ctypes.byref(z2)) == 0
+    assert lib.dr_view_zipn(2, arr(z2, va), ctypes.byref(z)) == L.DR_E_UNSUPPORTED  # zip of a zip
+    # a 2-ary zipn is a zip: zip_transform applies
+    zt = ctypes.c_void_p()
+    assert lib.dr_view_zip_transform(z2, L.DR_MUL, ctypes.byref(zt)) == 0
+    # trimmed leaves are allowed
+    d = ctypes.c_void_p()
+    assert lib.dr_view_drop(vb, 3, ctypes.byref(d)) == 0
+    assert lib.dr_view_zipn(2, arr(va, d), ctypes.byref(z)) == 0
+    size = ctypes.c_int64()
+    lib.dr_view_info(z, ctypes.byref(size), None, None, None)
+    assert size.value == 5
+
+
+def test_for_each_validation(lib):
+    F = {"copy": 0, "scale": 1, "add": 2, "triad": 3, "bs": 4}
+    vs = [view_of(make_vec([64], ptrs=[(i + 1) << 36])[1]) for i in range(5)]
+    arr = lambda *v: (ctypes.c_void_p * len(v))(*v)
+    z3 = ctypes.c_void_p()
+    assert lib.dr_view_zipn(3, arr(*vs[:3]), ctypes.byref(z3)) == 0
+    q = (ctypes.c_double * 2)(3.0, 0.2)
+    assert lib.dr_for_each(None, F["add"], q, 0, None) == L.DR_E_INVAL
+    assert lib.dr_for_each(z3, 9, q, 2, None) == L.DR_E_INVAL                  # unknown function
+    assert lib.dr_for_each(z3, F["copy"], q, 0, None) == L.DR_E_INVAL          # copy takes a 2-zip
+    assert lib.dr_for_each(z3, F["bs"], q, 2, None) == L.DR_E_INVAL            # black-scholes a 5-zip
+    assert lib.dr_for_each(z3, F["triad"], q, 0, None) == L.DR_E_INVAL         # triad needs q
+    assert lib.dr_for_each(vs[0], F["copy"], q, 0, None) == L.DR_E_INVAL       # not a zip
+    # integer vectors
+    iv = [view_of(make_vec([64], dtype=L.DR_I64, ptrs=[(i + 1) << 38])[1]) for i in range(2)]
+    zi = ctypes.c_void_p()
+    assert lib.dr_view_zipn(2, arr(*iv), ctypes.byref(zi)) == 0
+    assert lib.dr_for_each(zi, F["copy"], q, 0, None) == L.DR_E_DTYPE
+    # a written operand overlapping another operand without coinciding: rejected
+    _, hx = make_vec([64], ptrs=[1 << 40])
+    _, hy = make_vec([64], ptrs=[(1 << 40) + 4 * 8])   # 8 elements further into the same memory
+    zo = ctypes.c_void_p()
+    assert lib.dr_view_zipn(2, arr(view_of(hx), view_of(hy)), ctypes.byref(zo)) == 0
+    assert lib.dr_for_each(zo, F["copy"], q, 0, None) == L.DR_E_INVAL
+    # an empty zip launches nothing
+    ve = [view_of(make_vec([0], ptrs=[(i + 1) << 39])[1]) for i in range(3)]
+    ze = ctypes.c_void_p()
+    assert lib.dr_view_zipn(3, arr(*ve), ctypes.byref(ze)) == 0
+    assert lib.dr_for_each(ze, F["add"], q, 0, None) == L.DR_OK
+
+
+def test_transform_validation(lib):
+    _, ha = make_vec([32])
+    _, hb = make_vec([16], ptrs=[1 << 41])
+    _, hd = make_vec([32], dtype=L.DR_F64, ptrs=[1 << 42])
+    va = view_of(ha)
+    assert lib.dr_transform(va, hb, None) == L.DR_E_INVAL     # output too short
+    assert lib.dr_transform(va, hd, None) == L.DR_E_DTYPE
+    assert lib.dr_transform(va, None, None) == L.DR_E_INVAL
+    z = ctypes.c_void_p()
+    _, hc = make_vec([32], ptrs=[1 << 43])
+    assert lib.dr_view_zip(va, view_of(hc), ctypes.byref(z)) == 0
+    assert lib.dr_transform(z, hc, None) == L.DR_E_INVAL      # raw zip
+    _, hs = make_vec([32], ptrs=[(1 << 32) + 4])               # one element past a's start
+    assert lib.dr_transform(va, hs, None) == L.DR_E_INVAL     # partial overlap

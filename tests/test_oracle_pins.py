@@ -492,3 +492,19 @@ def test_black_scholes_zero_volatility_limit():
     K = X * np.exp(-r * T)
     assert np.allclose(call, np.maximum(S - K, 0), rtol=0, atol=1e-9)
     assert np.allclose(put, np.maximum(K - S, 0), rtol=0, atol=1e-9)
+
+
+def test_zip_bruteforce_k_agrees_with_pairwise_and_identity():
+    # k = 2 is the pairwise brute force; zipping a segmentation with itself k times
+    # returns that segmentation (minus its empty segments)
+    for la, lb in [([3, 5], [4, 4]), ([0, 4], [2, 0, 2]), ([5], [2, 1]), ([1, 1, 6], [8])]:
+        two = oracle.zip_segments_bruteforce(la, lb)
+        k = oracle.zip_segments_bruteforce_k([la, lb])
+        assert [(s[0], f[0], s[1], f[1], n) for s, f, n in k] == two
+    lens = [2, 0, 3, 1]
+    k3 = oracle.zip_segments_bruteforce_k([lens, lens, lens])
+    assert [n for _, _, n in k3] == [2, 3, 1]
+    assert [s for s, _, _ in k3] == [(0, 0, 0), (2, 2, 2), (3, 3, 3)]
+    # a third operand's cut splits a piece of the first two
+    k3 = oracle.zip_segments_bruteforce_k([[6], [6], [2, 4]])
+    assert [(s, f, n) for s, f, n in k3] == [((0, 0, 0), (0, 0, 0), 2), ((0, 0, 1), (2, 2, 0), 4)]

@@ -45,3 +45,26 @@ def stencil_f64_bound(steps: int, max_abs_u0: float) -> float:
     """fp32 vs FP64 after t steps: each step adds at most 3 roundings of values
     bounded by max|u0| (the 1/4-weighted update is a max-norm contraction)."""
     return 3.0 * steps * U32 * max_abs_u0
+
+
+def black_scholes_bound(S, X, T, r, sigma, aux, u=U32):
+    """First-order bound on |price - price*| for Black-Scholes evaluated in a
+    precision with unit roundoff u (fp32: 2^-24) from the same inputs, against
+    the FP64 values.  The kernel's quantities each carry a few roundings and
+    one library call (log <= 1 ulp, exp <= 2 ulp, erfc <= 4 ulp for fp32; sqrt
+    and division correctly rounded), so 8u bounds each one's relative error:
+      d1:   E1 = 8u (1 + |ln(S/X)| + (r + sigma^2/2) T) / (sigma sqrt T) + 8u |d1|
+      d2:   E2 = E1 + 8u sigma sqrt T
+      N:    8u absolute (N = 1 - e or e with e = erfc(.)/2 <= 1/2)
+      K = X e^{-rT}:  8u (1 + rT) K
+    and a price S N(+-d1) -+ K N(+-d2) moves by at most the density times the
+    argument's error plus N's own error, per term, plus the final 2 roundings.
+    aux is the oracle's (phi(d1), phi(d2), d1, K) per option."""
+    import numpy as np
+    S, X, T = (np.asarray(v, np.float64) for v in (S, X, T))
+    phi1, phi2, d1, K = aux[:, 0], aux[:, 1], aux[:, 2], aux[:, 3]
+    s = sigma * np.sqrt(T)
+    e1 = 8 * u * (1 + np.abs(np.log(S / X)) + (r + 0.5 * sigma * sigma) * T) / s + 8 * u * np.abs(d1)
+    e2 = e1 + 8 * u * s
+    eK = 8 * u * (1 + r * T) * K
+    return S * (phi1 * e1 + 8 * u) + K * (phi2 * e2 + 8 * u) + eK + 4 * u * (S + K)
