@@ -301,7 +301,12 @@ def measure_rows(api, dev, s, peak) -> dict:
     r32, sig32 = float(np.float32(inputs.BS_R)), float(np.float32(inputs.BS_SIGMA))
     ms = _time(lambda: api.for_each(zbs, "black_scholes", r32, sig32, stream=s), s, 20)
     api.sync_status(s)
+    try:
+        bs_traffic = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get("black_scholes")
+    except (OSError, ValueError):
+        bs_traffic = None
     rows["black_scholes_f32_2^28_8segs"] = _row(ms, 20 * n, peak, options_per_s=n / (ms / 1e3),
+                                                traffic=bs_traffic,
                                                 note="S, X, T read; call, put written: 20 B/option")
     del zbs, bs, S, X, Tm
 
@@ -365,6 +370,9 @@ def main() -> None:
     ap.add_argument("--log2n", type=int, default=28, help="headline size 2^log2n (profiling captures use less)")
     ap.add_argument("--stencil-only", type=int, default=0, metavar="N",
                     help="profiling helper: only run the stencil on an N x N grid (8 row blocks), 5 steps")
+    ap.add_argument("--foreach-only", default="", metavar="FN",
+                    help="profiling helper: only run for_each FN (copy, scale, add, triad: fp64; "
+                         "black_scholes: fp32) over 2^log2n elements in 8 segments, 5 times")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -377,6 +385,28 @@ def main() -> None:
     global N_ELEMS
     N_ELEMS = 1 << args.log2n
     build.build()
+    if args.foreach_only:
+        fn, n = args.foreach_only, N_ELEMS
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        lens = [n // 8] * 8
+        if fn == "black_scholes":
+            vs = [api.SegmentedVector.from_tensor(torch.from_numpy(v).to(dev), lens)
+                  for v in inputs.black_scholes_inputs(n)]
+            vs += [api.SegmentedVector.empty(lens, torch.float32, dev) for _ in range(2)]
+            fargs, nbytes = (float(np.float32(inputs.BS_R)), float(np.float32(inputs.BS_SIGMA))), 20 * n
+        else:
+            vs = [api.SegmentedVector.from_tensor(torch.from_numpy(v).to(dev), lens)
+                  for v in inputs.stream_inputs(n, np.float64)]
+            sel = {"copy": (0, 2), "scale": (1, 2), "add": (0, 1, 2), "triad": (0, 1, 2)}[fn]
+            vs = [vs[i] for i in sel]
+            fargs = (3.0,) if fn in ("scale", "triad") else ()
+            nbytes = {"copy": 16, "scale": 16, "add": 24, "triad": 24}[fn] * n
+        z = api.View.zipn(*vs)
+        s = torch.cuda.current_stream()
+        ms = _time(lambda: api.for_each(z, fn, *fargs, stream=s), s, 5)
+        api.sync_status(s)
+        print(json.dumps({"for_each": fn, "n": n, "ms": ms, "GB/s": nbytes / (ms / 1e3) / 1e9}))
+        return
     if args.stencil_only:
         n = args.stencil_only
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
