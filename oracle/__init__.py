@@ -57,6 +57,11 @@ _SIGS = {
     "oracle_stream_f32": (None, [ctypes.c_int, _I64, _P, _P, _P, ctypes.c_float]),
     "oracle_stream_f64": (None, [ctypes.c_int, _I64, _P, _P, _P, ctypes.c_double]),
     "oracle_black_scholes_f64": (None, [_I64, _P, _P, _P, ctypes.c_double, ctypes.c_double, _P, _P, _P]),
+    "oracle_sort_f32": (None, [_P, _I64]),
+    "oracle_sort_f64": (None, [_P, _I64]),
+    "oracle_sort_i32": (None, [_P, _I64]),
+    "oracle_sort_i64": (None, [_P, _I64]),
+    "oracle_partition_sort_i64": (None, [ctypes.c_int, _P, _P, _P]),
 }
 
 
@@ -314,3 +319,28 @@ def black_scholes_f64(S, X, T, r: float, sigma: float, aux: bool = False):
     lib().oracle_black_scholes_f64(S.size, _p(S), _p(X), _p(T), float(r), float(sigma), _p(call), _p(put),
                                    _p(ax) if aux else None)
     return (call, put, ax) if aux else (call, put)
+
+
+# ---------------------------------------------------------------------------
+# sort (Sec. 4.3 "sort")
+# ---------------------------------------------------------------------------
+
+_SORTS = {np.dtype(np.float32): "oracle_sort_f32", np.dtype(np.float64): "oracle_sort_f64",
+          np.dtype(np.int32): "oracle_sort_i32", np.dtype(np.int64): "oracle_sort_i64"}
+
+
+def sort(x) -> np.ndarray:
+    """Ascending sort of the concatenation; floats in IEEE totalOrder."""
+    x = np.array(x, copy=True)
+    getattr(lib(), _SORTS[x.dtype])(_p(x), x.size)
+    return x
+
+
+def partition_sort_i64(lens, x) -> np.ndarray:
+    """The paper's distributed partition sort, step by step (int64)."""
+    lens = _c(lens, np.int64)
+    x = _c(x, np.int64)
+    assert int(lens.sum()) == x.size
+    out = np.empty_like(x)
+    lib().oracle_partition_sort_i64(int(lens.size), _p(lens), _p(x), _p(out))
+    return out

@@ -339,4 +339,89 @@ void oracle_black_scholes_f64(int64_t n, const double* S, const double* X, const
   }
 }
 
+// --------------------------------------------------------------------------
+// sort (Sec. 4.3 "sort"): the elements of the range in ascending order,
+// written back over the same segmentation (C++'s sort is in place).  The plain
+// definition is a sort of the concatenation.  Floating-point keys use the IEEE
+// 754 totalOrder (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN, NaNs by
+// payload), so that the sorted sequence is unique bit for bit.
+// --------------------------------------------------------------------------
+}  // extern "C"
+
+static bool total_less_f64(double a, double b) {
+  int64_t x, y;
+  std::memcpy(&x, &a, 8);
+  std::memcpy(&y, &b, 8);
+  // negative values order by decreasing magnitude bits
+  if (x < 0) x = INT64_MIN - x - 1;  // maps sign-magnitude to two's complement order
+  if (y < 0) y = INT64_MIN - y - 1;
+  return x < y;
+}
+static bool total_less_f32(float a, float b) {
+  int32_t x, y;
+  std::memcpy(&x, &a, 4);
+  std::memcpy(&y, &b, 4);
+  if (x < 0) x = INT32_MIN - x - 1;
+  if (y < 0) y = INT32_MIN - y - 1;
+  return x < y;
+}
+
+extern "C" {
+
+void oracle_sort_f32(float* x, int64_t n) { std::sort(x, x + n, total_less_f32); }
+void oracle_sort_f64(double* x, int64_t n) { std::sort(x, x + n, total_less_f64); }
+void oracle_sort_i32(int32_t* x, int64_t n) { std::sort(x, x + n); }
+void oracle_sort_i64(int64_t* x, int64_t n) { std::sort(x, x + n); }
+
+// The paper's distributed partition sort written out step by step for int64
+// over p segments (lens[k] elements each, concatenated in x; result in out, the
+// same segmentation):
+//   1. each segment is sorted in place;
+//   2. p-1 "medians" are taken from every sorted segment: the elements at
+//      ranks floor(j * len / p), j = 1..p-1 (none from an empty segment);
+//   3. all samples are sorted and the p-1 splitters are taken at ranks
+//      floor(j * m / p), j = 1..p-1, of the m samples;
+//   4. every segment counts its elements per chunk: chunk c (0 <= c < p) holds
+//      the values v with splitter[c-1] <= v < splitter[c] (open ends at 0 and
+//      p-1); the counts summed over segments give each chunk's size;
+//   5. the elements are redistributed into the chunks (segment order within a
+//      chunk), each chunk is sorted, and the chunks, concatenated in order,
+//      are copied into the output range.
+void oracle_partition_sort_i64(int p, const int64_t* lens, const int64_t* x, int64_t* out) {
+  std::vector<std::vector<int64_t>> seg(p);
+  int64_t off = 0;
+  for (int k = 0; k < p; ++k) {
+    seg[k].assign(x + off, x + off + lens[k]);
+    off += lens[k];
+    std::sort(seg[k].begin(), seg[k].end());
+  }
+  std::vector<int64_t> samples;
+  for (int k = 0; k < p; ++k) {
+    const int64_t L = (int64_t)seg[k].size();
+    if (L == 0) continue;
+    for (int j = 1; j < p; ++j) samples.push_back(seg[k][(j * L) / p]);
+  }
+  std::sort(samples.begin(), samples.end());
+  const int64_t m = (int64_t)samples.size();
+  std::vector<int64_t> split;
+  if (m > 0)
+    for (int j = 1; j < p; ++j) split.push_back(samples[(j * m) / p]);
+  const int nchunk = (int)split.size() + 1;
+  auto chunk_of = [&](int64_t v) {
+    return (int)(std::upper_bound(split.begin(), split.end(), v) - split.begin());
+  };
+  std::vector<int64_t> size(nchunk, 0);
+  for (int k = 0; k < p; ++k)
+    for (int64_t v : seg[k]) size[chunk_of(v)]++;
+  std::vector<std::vector<int64_t>> chunk(nchunk);
+  for (int c = 0; c < nchunk; ++c) chunk[c].reserve(size[c]);
+  for (int k = 0; k < p; ++k)
+    for (int64_t v : seg[k]) chunk[chunk_of(v)].push_back(v);
+  int64_t o = 0;
+  for (int c = 0; c < nchunk; ++c) {
+    std::sort(chunk[c].begin(), chunk[c].end());
+    for (int64_t v : chunk[c]) out[o++] = v;
+  }
+}
+
 }  // extern "C"

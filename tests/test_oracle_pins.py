@@ -508,3 +508,56 @@ def test_zip_bruteforce_k_agrees_with_pairwise_and_identity():
     # a third operand's cut splits a piece of the first two
     k3 = oracle.zip_segments_bruteforce_k([[6], [6], [2, 4]])
     assert [(s, f, n) for s, f, n in k3] == [((0, 0, 0), (0, 0, 0), 2), ((0, 0, 1), (2, 2, 0), 4)]
+
+
+# ----------------------------------------------------------------------------------
+# sort: plain definition (ascending; floats in IEEE totalOrder) and the paper's
+# distributed partition sort
+# ----------------------------------------------------------------------------------
+
+def test_sort_total_order_of_special_values():
+    # totalOrder: -NaN < -inf < -1 < -tiny < -0 < +0 < tiny < 1 < inf < +NaN
+    for dt, it in [(np.float32, np.uint32), (np.float64, np.uint64)]:
+        vals = np.array([np.nan, 1.0, -0.0, np.inf, -1.0, 0.0, -np.inf, -np.nan], dt)
+        tiny = np.finfo(dt).smallest_subnormal
+        vals = np.concatenate([vals, np.array([tiny, -tiny], dt)])
+        neg_nan = (-np.abs(np.array([np.nan], dt)))  # sign bit set
+        vals[-3] = neg_nan[0]
+        want = np.array([neg_nan[0], -np.inf, -1.0, -tiny, -0.0, 0.0, tiny, 1.0, np.inf, np.nan], dt)
+        got = oracle.sort(vals[np.argsort(np.arange(vals.size) * 7 % vals.size)])
+        assert np.array_equal(got.view(it), want.view(it))
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.int64, np.float32, np.float64])
+def test_sort_is_sorted_permutation(dt):
+    n = 5000
+    if dt in (np.int32, np.int64):
+        x = inputs.uniform_int64(RNG_KEY, n, -300, 300).astype(dt)       # many duplicates
+    else:
+        x = inputs.uniform_pm1_f32(RNG_KEY, n).astype(dt)
+    y = oracle.sort(x)
+    assert np.all(y[1:] >= y[:-1])
+    assert np.array_equal(np.sort(y), np.sort(x))     # same multiset (library sort as a check)
+    assert np.array_equal(y, np.sort(x))              # no NaN / signed zero: plain order agrees
+
+
+def test_sort_bruteforce_permutations():
+    base = [3, -1, 3, 0, 7, -1]
+    for perm in itertools.permutations(range(len(base))):
+        x = np.array([base[i] for i in perm], np.int64)
+        assert list(oracle.sort(x)) == sorted(base)
+
+
+@pytest.mark.parametrize("trial", range(12))
+def test_partition_sort_equals_plain_sort(trial):
+    # the paper's splitter / histogram / redistribute / local-sort procedure reaches the
+    # plain definition for any segmentation, duplicates, empty segments and one segment
+    n = [0, 1, 7, 100, 1000, 5000][trial % 6]
+    p = 1 + trial % 9
+    lens = inputs.random_cut_segments(500 + trial, n, p) if n else [0] * p
+    if trial % 4 == 1:
+        lens = [0] + lens + [0]
+    span = 10 if trial % 3 == 0 else 1_000_000
+    x = inputs.uniform_int64(600 + trial, n, -span, span)
+    assert np.array_equal(oracle.partition_sort_i64(lens, x), np.sort(x))
+    assert np.array_equal(oracle.partition_sort_i64(lens, np.full(n, 5, np.int64)), np.full(n, 5))
