@@ -310,6 +310,26 @@ def measure_rows(api, dev, s, peak) -> dict:
                                                 note="S, X, T read; call, put written: 20 B/option")
     del zbs, bs, S, X, Tm
 
+    # sort: 2^28 fp32 keys U[-1, 1) in 8 segments, into another 8-segment vector.
+    # Radix sort traffic: one histogram read + 4 passes of read + write = 36 B/key
+    # (the minimum any sort needs is 8 B/key: one read, one write).
+    x = torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_SORT, n)).to(dev)
+    vin = api.SegmentedVector.from_tensor(x, lens)
+    vout = api.SegmentedVector.empty(lens, torch.float32, dev)
+    ms = _time(lambda: api.sort(vin, vout, stream=s), s, 10)
+    api.sync_status(s)
+    rows["sort_f32_2^28_8segs"] = _row(ms, 36 * n, peak, keys_per_s=n / (ms / 1e3),
+                                       note="GB/s over the radix sort's 36 B/key (histogram + 4 passes)")
+    del vin, vout, x
+    xi = torch.from_numpy(inputs.raw_u64(inputs.SEED_SORT + 1, n // 2).view(np.int64)).to(dev)
+    vin = api.SegmentedVector.from_tensor(xi, [n // 16] * 8)
+    vout = api.SegmentedVector.empty([n // 16] * 8, torch.int64, dev)
+    ms = _time(lambda: api.sort(vin, vout, stream=s), s, 5)
+    api.sync_status(s)
+    rows["sort_i64_2^27_8segs"] = _row(ms, 136 * (n // 2), peak, keys_per_s=(n // 2) / (ms / 1e3),
+                                       note="GB/s over 136 B/key (histogram + 8 passes of 16 B)")
+    del vin, vout, xi
+
     # autograd: scan n = 2^26 in 8 segments, fwd + bwd (reverse scan)
     n = 1 << 26
     xs = [q.clone().requires_grad_(True) for q in
@@ -370,6 +390,8 @@ def main() -> None:
     ap.add_argument("--log2n", type=int, default=28, help="headline size 2^log2n (profiling captures use less)")
     ap.add_argument("--stencil-only", type=int, default=0, metavar="N",
                     help="profiling helper: only run the stencil on an N x N grid (8 row blocks), 5 steps")
+    ap.add_argument("--sort-only", action="store_true",
+                    help="profiling helper: only sort 2^log2n fp32 keys in 8 segments, 5 times")
     ap.add_argument("--foreach-only", default="", metavar="FN",
                     help="profiling helper: only run for_each FN (copy, scale, add, triad: fp64; "
                          "black_scholes: fp32) over 2^log2n elements in 8 segments, 5 times")
@@ -385,6 +407,19 @@ def main() -> None:
     global N_ELEMS
     N_ELEMS = 1 << args.log2n
     build.build()
+    if args.sort_only:
+        n = N_ELEMS
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        lens = [n // 8] * 8
+        x = torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_SORT, n)).to(dev)
+        vin = api.SegmentedVector.from_tensor(x, lens)
+        vout = api.SegmentedVector.empty(lens, torch.float32, dev)
+        s = torch.cuda.current_stream()
+        ms = _time(lambda: api.sort(vin, vout, stream=s), s, 5)
+        api.sync_status(s)
+        print(json.dumps({"sort": "f32", "n": n, "ms": ms, "Gkeys/s": n / (ms / 1e3) / 1e9,
+                          "GB/s_36B": 36 * n / (ms / 1e3) / 1e9}))
+        return
     if args.foreach_only:
         fn, n = args.foreach_only, N_ELEMS
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))

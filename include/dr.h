@@ -288,6 +288,22 @@ int dr_for_each(const dr_view* zip, int fn, const double* args, int nargs, dr_st
  * is DR_E_INVAL.  One launch, no workspace, graph-capturable. */
 int dr_transform(const dr_view* in, dr_vec* out, dr_stream_t stream);
 
+/* sort (Sec. 4.3 "sort"): out_0 <= out_1 <= ... <= out_{n-1} are the n = |in|
+ * elements of the single-valued view `in` (its transforms evaluated) in
+ * ascending order, written over out's segments (its first n elements).
+ * Integers by value; fp32 / fp64 by the IEEE 754 totalOrder (-NaN < -inf <
+ * ... < -0 < +0 < ... < +inf < +NaN, NaNs by payload), so the result is
+ * unique bit for bit.  out may be the storage of in's vector (in place, as
+ * C++'s sort).  n <= 2^30 - 1 (DR_E_UNSUPPORTED beyond).  The paper sorts with
+ * a distributed partition sort (sampled splitters, per-chunk counts,
+ * redistribution, local sorts); on one GPU the partition is a radix pass, so
+ * this is a least-significant-digit radix sort over the segment table: one
+ * histogram read plus one pass per 8-bit digit (4 passes for 32-bit keys, 8 for
+ * 64-bit), each pass one kernel with decoupled lookback.  The view's workspace
+ * holds two scratch copies of the keys plus counters (allocated by the first
+ * call, as for dr_inclusive_scan); each call clears its counters on `stream`. */
+int dr_sort(const dr_view* in, dr_vec* out, dr_stream_t stream);
+
 /* The dot product of dr_transform_reduce(zip(x, y) | DR_MUL, DR_PLUS) for callers
  * that cannot allocate device memory at the call (a framework that owns all device
  * memory through its own pool; a latency-critical loop that cannot pay for

@@ -14,7 +14,7 @@ import importlib
 _API = ("SegmentedVector", "View", "MdArray", "Batch", "inclusive_scan", "exclusive_scan",
         "reverse_inclusive_scan", "transform_reduce", "scale_by_partner", "stencil5", "stencil5_T", "stencil5_T_wgrad",
         "sync_status", "set_spin_limit", "debug_skip_publish", "block_lengths", "dot_view", "stream_handle",
-        "for_each", "transform", "FOR_EACH_FNS")
+        "for_each", "transform", "FOR_EACH_FNS", "sort")
 
 
 def __getattr__(name):

@@ -85,6 +85,7 @@ PROTOTYPES = {
     "dr_scale_by_partner": (_I, [_P, _P, _P, _P, _P, _P]),
     "dr_for_each": (_I, [_P, _I, ctypes.POINTER(_D), _I, _P]),
     "dr_transform": (_I, [_P, _P, _P]),
+    "dr_sort": (_I, [_P, _P, _P]),
     "dr_dot_f32_noalloc": (_I, [_I, _PI64, _PP, _PP, ctypes.c_float, _P, _P]),
     "dr_stencil5": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "dr_stencil5_T": (_I, [_P, _P, _P, _I, _D, _D, _P]),

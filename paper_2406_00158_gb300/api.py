@@ -294,6 +294,14 @@ def transform(inp, out: SegmentedVector, stream=None) -> SegmentedVector:
     return out
 
 
+def sort(inp, out: SegmentedVector, stream=None) -> SegmentedVector:
+    """out = the elements of inp in ascending order (floats in IEEE totalOrder);
+    out may be inp's own vector (in place)."""
+    v = _as_view(inp)
+    call("dr_sort", v.handle, out.handle, stream_handle(stream))
+    return out
+
+
 def scale_by_partner(x: SegmentedVector, y: SegmentedVector, g: torch.Tensor, gx: Optional[SegmentedVector],
                      gy: Optional[SegmentedVector], stream=None) -> None:
     call("dr_scale_by_partner", x.handle, y.handle, ctypes.c_void_p(g.data_ptr()),

@@ -822,6 +822,60 @@ extern "C" int dr_transform(const dr_view* in, dr_vec* out, dr_stream_t stream) 
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
 }
 
+extern "C" int dr_sort(const dr_view* in_c, dr_vec* out, dr_stream_t stream) {
+  clear_error();
+  const char* who = "dr_sort";
+  if (int r = check_single(in_c, who)) return r;
+  dr_view* in = const_cast<dr_view*>(in_c);
+  if (!out) return fail(DR_E_INVAL, "%s: NULL output", who);
+  if (out->dtype != in->dtype) return fail(DR_E_DTYPE, "%s: output dtype differs from input", who);
+  if (out->n < in->size)
+    return fail(DR_E_INVAL, "%s: output has %lld elements, input %lld", who, (long long)out->n, (long long)in->size);
+  const int64_t n = in->size;
+  if (n == 0) return DR_OK;
+  if (n >= (int64_t(1) << 30)) return fail(DR_E_UNSUPPORTED, "%s: %lld elements (limit 2^30 - 1)", who, (long long)n);
+  cudaStream_t s = (cudaStream_t)stream;
+  static thread_local SortParams p;
+  std::memset(&p, 0, sizeof p);
+  p.vc = in->code();
+  p.dtype = in->dtype;
+  p.n = n;
+  SortLaunch L{};
+  if (int r = call_pieces(in, nullptr, sort_tile_elems(in->dtype), p.in, &p.npin, &L.ntiles0)) return r;
+  const std::vector<Seg> os = out->window(0, n);
+  if ((int)os.size() > kMaxPieces) return fail(DR_E_UNSUPPORTED, "%s: output has more than %d segments", who, kMaxPieces);
+  int64_t g = 0;
+  for (size_t i = 0; i < os.size(); ++i) {
+    p.out[i].p = os[i].p;
+    p.out[i].start = g;
+    g += os[i].len;
+  }
+  p.npout = (int)os.size();
+  const int tile = sort_tile_elems(in->dtype), esz = esize(in->dtype);
+  L.ntiles = (n + tile - 1) / tile;
+  const int64_t maxt = std::max(L.ntiles0, L.ntiles);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const int64_t ncounts = 256 * maxt;
+  const size_t scan_b = up(scan_ws_bytes((ncounts + scan_tile_elems(DR_I32) - 1) / scan_tile_elems(DR_I32), DR_I32));
+  const size_t counts_b = up((size_t)ncounts * 4), tmp_b = up((size_t)n * esz);
+  // the scan's workspace comes first so that it keeps its (self-cleaning) state when
+  // the workspace is reused; it is zeroed once, when allocated
+  if (int r = in->ws_sort.ensure(scan_b + counts_b + 2 * tmp_b, s)) return r;
+  char* ws = static_cast<char*>(in->ws_sort.ptr);
+  L.scan_ws = ws;
+  p.counts = reinterpret_cast<unsigned*>(ws + scan_b);
+  L.tmp[0] = ws + scan_b + counts_b;
+  L.tmp[1] = L.tmp[0] + tmp_b;
+  static thread_local ScanParams sp;
+  L.scan = &sp;
+  p.status = status_word();
+  if (!p.status) return fail(DR_E_CUDA, "%s: no device status word", who);
+  p.spin_limit = spin_limit();
+  cudaError_t e = cudaSuccess;
+  e = launch_sort(p, L, s);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
+}
+
 static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
                       cudaStream_t s, const dr_md2* prev = nullptr, double* acc = nullptr) {
   clear_error();

@@ -96,7 +96,7 @@ struct dr_view {
   double post_arg[dr::kMaxChain];
   int64_t size = 0;
   std::vector<dr::Piece> pieces;  // re-segmentation of the leaves' windows
-  dr::Workspace ws_scan, ws_reduce;
+  dr::Workspace ws_scan, ws_reduce, ws_sort;
 
   void recompute();
   dr::KViewCode code() const;

@@ -126,6 +126,38 @@ struct TransformParams {
   KPiece pc[kMaxPieces];
 };
 
+// sort: input view pieces (first pass and histogram), output segments (last
+// pass), and the scratch of the current pass.
+struct SortOut {
+  char* p;
+  int64_t start;  // global index of the segment's first element
+};
+
+struct SortParams {
+  KViewCode vc;
+  int dtype;
+  int npin;
+  int npout;
+  int pass;            // digit index: bits [8 pass, 8 pass + 8)
+  int64_t n;
+  int64_t ntiles;      // tiles of this launch
+  const char* src;     // key bits of the previous pass (contiguous)
+  char* dst;           // key bits of this pass (contiguous; not on the last pass)
+  unsigned* counts;    // [256][ntiles] per-tile digit counts, then their exclusive scan
+  unsigned* status;
+  int64_t spin_limit;
+  KPiece in[kMaxPieces];
+  SortOut out[kMaxPieces];
+};
+
+struct SortLaunch {
+  int64_t ntiles0;     // tiles of the first pass (per-piece tiling of the view)
+  int64_t ntiles;      // tiles of the other passes (ceil(n / tile))
+  char* tmp[2];        // two contiguous scratch buffers of n keys
+  char* scan_ws;       // workspace of the counts' scan (self-cleaning; zeroed once)
+  ScanParams* scan;    // host scratch for the scan's parameters
+};
+
 struct StencilSeg {
   const float* in;   // allocation incl. ghost rows: (rows + 2) * cols
   const float* prev; // weight-gradient step only: the forward state u_{t-1} (same layout)
@@ -163,6 +195,8 @@ int reduce_tile_elems(int dtype);
 int scan_tile_elems(int dtype);
 int scale_tile_elems();
 int foreach_tile_elems(int dtype);  // for_each and transform
+int sort_tile_elems(int dtype);
+int sort_passes(int dtype);
 #ifndef DR_STENCIL_ROWS
 #define DR_STENCIL_ROWS 64
 #endif
@@ -180,6 +214,7 @@ cudaError_t launch_stencil(const StencilParams& p, cudaStream_t s);
 cudaError_t launch_halo(const HaloParams& p, cudaStream_t s);
 cudaError_t launch_for_each(const ForEachParams& p, cudaStream_t s);
 cudaError_t launch_transform(const TransformParams& p, cudaStream_t s);
+cudaError_t launch_sort(SortParams& p, const SortLaunch& L, cudaStream_t s);
 
 // Resident-CTA count helpers (host).
 int reduce_grid(int dtype);

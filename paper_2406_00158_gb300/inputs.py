@@ -43,6 +43,7 @@ SEED_BATCH_X = 3411   # batch values x
 SEED_BATCH_P = 4411   # batch partner values p
 SEED_STREAM = 2412    # STREAM arrays a, b, c: streams 2412, 2413, 2414
 SEED_BS = 2415        # Black-Scholes S, X, T: streams 2415, 2416, 2417
+SEED_SORT = 2418      # sort keys
 
 # Black-Scholes option batch (the paper gives no sizes or ranges): spot S in
 # [5, 30), strike X in [1, 100), expiry T in [0.25, 10) years, fp32; rate and

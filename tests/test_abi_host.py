@@ -296,3 +296,21 @@ def test_transform_validation(lib):
     assert lib.dr_transform(z, hc, None) == L.DR_E_INVAL      # raw zip
     _, hs = make_vec([32], ptrs=[(1 << 32) + 4])               # one element past a's start
     assert lib.dr_transform(va, hs, None) == L.DR_E_INVAL     # partial overlap
+
+
+def test_sort_validation(lib):
+    _, ha = make_vec([32])
+    _, hb = make_vec([16], ptrs=[1 << 41])
+    _, hd = make_vec([32], dtype=L.DR_F64, ptrs=[1 << 42])
+    va = view_of(ha)
+    assert lib.dr_sort(va, hb, None) == L.DR_E_INVAL      # output too short
+    assert lib.dr_sort(va, hd, None) == L.DR_E_DTYPE
+    assert lib.dr_sort(va, None, None) == L.DR_E_INVAL
+    z = ctypes.c_void_p()
+    assert lib.dr_view_zip(va, view_of(hb), ctypes.byref(z)) == 0
+    assert lib.dr_sort(z, ha, None) == L.DR_E_INVAL       # raw zip
+    _, he = make_vec([0])
+    assert lib.dr_sort(view_of(he), he, None) == L.DR_OK  # nothing to sort, no launch
+    big = [1 << 29, 1 << 29]                                # 2^30 elements: beyond the counters
+    _, hbig = make_vec(big, ptrs=fake_ptrs(big, base=1 << 44))
+    assert lib.dr_sort(view_of(hbig), hbig, None) == L.DR_E_UNSUPPORTED
