@@ -179,16 +179,27 @@ KViewCode dr_view::code() const {
   c.nleaf = nleaf;
   c.zipop = zipop < 0 ? DR_PLUS : zipop;
   c.npost = npost;
+  // integer views take the scalar truncated toward zero (as a C cast), fp32 views rounded
+  auto to_i = [](double v) {
+    if (!(v == v)) return 0LL;
+    if (v >= 9.2233720368547758e18) return (long long)0x7fffffffffffffffLL;
+    if (v <= -9.2233720368547758e18) return (long long)0x8000000000000000LL;
+    return (long long)v;
+  };
   for (int l = 0; l < 2; ++l) {
     c.npre[l] = npre[l];
     for (int k = 0; k < kMaxChain; ++k) {
       c.pre_op[l][k] = pre_op[l][k];
       c.pre_arg[l][k] = pre_arg[l][k];
+      c.pre_argf[l][k] = (float)pre_arg[l][k];
+      c.pre_argi[l][k] = to_i(pre_arg[l][k]);
     }
   }
   for (int k = 0; k < kMaxChain; ++k) {
     c.post_op[k] = post_op[k];
     c.post_arg[k] = post_arg[k];
+    c.post_argf[k] = (float)post_arg[k];
+    c.post_argi[k] = to_i(post_arg[k]);
   }
   if (nleaf == 1 && npre[0] == 0 && npost == 0) c.kind = 0;
   else if (nleaf == 2 && zipop == DR_MUL && npre[0] == 0 && npre[1] == 0 && npost == 0) c.kind = 1;

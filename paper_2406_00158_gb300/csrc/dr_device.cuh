@@ -95,45 +95,102 @@ __device__ __forceinline__ T unop_rt(int op, T x, T a) {
 }
 
 // The fused view of a kernel: nleaf operands, each with a chain of unary ops,
-// combined by zipop (if two), then a chain of unary ops.
+// combined by zipop (if two), then a chain of unary ops.  The view code stays
+// where the launch put it (the kernel's __grid_constant__ parameters): its
+// fields are uniform across the grid and read from there, so evaluating a view
+// costs no registers beyond the values themselves.
+template <typename T>
+__device__ __forceinline__ T view_arg(const double* d, const float* f, const long long* i, int k) {
+  if constexpr (sizeof(T) == 4 && T(0.5) != T(0)) return f[k];       // float
+  else if constexpr (T(0.5) != T(0)) return d[k];                    // double
+  else return (T)i[k];                                               // int, long long
+}
+
+// One op applied to N register values (the switch taken once for all of them);
+// the same arithmetic as unop_rt / binop_rt.
+template <typename T, int N>
+__device__ __forceinline__ void unop_all(int op, T a, T* x) {
+  switch (op) {
+    case DR_U_SCALE:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = wrap_mul(a, x[i]);
+      break;
+    case DR_U_ADD:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = wrap_add(x[i], a);
+      break;
+    case DR_U_NEG:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = wrap_mul(T(-1), x[i]);
+      break;
+    case DR_U_ABS:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = x[i] < T(0) ? wrap_mul(T(-1), x[i]) : x[i];
+      break;
+    default:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = wrap_mul(x[i], x[i]);
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void binop_all(int op, T* x, const T* y) {
+  switch (op) {
+    case DR_PLUS:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = wrap_add(x[i], y[i]);
+      break;
+    case DR_MUL:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = wrap_mul(x[i], y[i]);
+      break;
+    case DR_MIN:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = y[i] < x[i] ? y[i] : x[i];
+      break;
+    default:
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = x[i] < y[i] ? y[i] : x[i];
+  }
+}
+
 template <typename T>
 struct ViewEval {
-  int nleaf, zipop, npre[2], npost;
-  int pre_op[2][kMaxChain], post_op[kMaxChain];
-  T pre_arg[2][kMaxChain], post_arg[kMaxChain];
+  const KViewCode* c;
 
-  __device__ __forceinline__ void init(const KViewCode& c) {
-    nleaf = c.nleaf;
-    zipop = c.zipop;
-    npost = c.npost;
-#pragma unroll
-    for (int l = 0; l < 2; ++l) {
-      npre[l] = c.npre[l];
-#pragma unroll
-      for (int k = 0; k < kMaxChain; ++k) {
-        pre_op[l][k] = c.pre_op[l][k];
-        pre_arg[l][k] = (T)c.pre_arg[l][k];
-      }
+  __device__ __forceinline__ void init(const KViewCode& code) { c = &code; }
+
+  // The view over N values of each leaf held in registers: a (leaf 0) becomes
+  // the view's values; b (leaf 1, used when the view has two leaves) is scratch.
+  // Op by op over the whole array, so a chain costs one branch per op per call.
+  template <int N>
+  __device__ __forceinline__ void eval_all(T* a, T* b) const {
+#pragma unroll 1
+    for (int k = 0; k < c->npre[0]; ++k)
+      unop_all<T, N>(c->pre_op[0][k], view_arg<T>(c->pre_arg[0], c->pre_argf[0], c->pre_argi[0], k), a);
+    if (c->nleaf == 2) {
+#pragma unroll 1
+      for (int k = 0; k < c->npre[1]; ++k)
+        unop_all<T, N>(c->pre_op[1][k], view_arg<T>(c->pre_arg[1], c->pre_argf[1], c->pre_argi[1], k), b);
+      binop_all<T, N>(c->zipop, a, b);
     }
-#pragma unroll
-    for (int k = 0; k < kMaxChain; ++k) {
-      post_op[k] = c.post_op[k];
-      post_arg[k] = (T)c.post_arg[k];
-    }
+#pragma unroll 1
+    for (int k = 0; k < c->npost; ++k)
+      unop_all<T, N>(c->post_op[k], view_arg<T>(c->post_arg, c->post_argf, c->post_argi, k), a);
   }
   __device__ __forceinline__ T operator()(T a, T b) const {
 #pragma unroll
     for (int k = 0; k < kMaxChain; ++k)
-      if (k < npre[0]) a = unop_rt(pre_op[0][k], a, pre_arg[0][k]);
-    if (nleaf == 2) {
+      if (k < c->npre[0]) a = unop_rt(c->pre_op[0][k], a, view_arg<T>(c->pre_arg[0], c->pre_argf[0], c->pre_argi[0], k));
+    if (c->nleaf == 2) {
 #pragma unroll
       for (int k = 0; k < kMaxChain; ++k)
-        if (k < npre[1]) b = unop_rt(pre_op[1][k], b, pre_arg[1][k]);
-      a = binop_rt(zipop, a, b);
+        if (k < c->npre[1])
+          b = unop_rt(c->pre_op[1][k], b, view_arg<T>(c->pre_arg[1], c->pre_argf[1], c->pre_argi[1], k));
+      a = binop_rt(c->zipop, a, b);
     }
 #pragma unroll
     for (int k = 0; k < kMaxChain; ++k)
-      if (k < npost) a = unop_rt(post_op[k], a, post_arg[k]);
+      if (k < c->npost) a = unop_rt(c->post_op[k], a, view_arg<T>(c->post_arg, c->post_argf, c->post_argi, k));
     return a;
   }
 };

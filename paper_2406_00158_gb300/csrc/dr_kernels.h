@@ -29,6 +29,11 @@ struct KViewCode {
   int post_op[kMaxChain];
   double pre_arg[2][kMaxChain];
   double post_arg[kMaxChain];
+  // the same scalars converted once on the host for fp32 and integer views
+  float pre_argf[2][kMaxChain];
+  float post_argf[kMaxChain];
+  long long pre_argi[2][kMaxChain];
+  long long post_argi[kMaxChain];
 };
 
 // One piece of a call: `len` elements, operands at a / b, output at o (byte

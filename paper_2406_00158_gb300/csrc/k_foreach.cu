@@ -280,12 +280,28 @@ __global__ void __launch_bounds__(FT) k_transform(const __grid_constant__ Transf
         av[c] = ld16_stream<T>(pc.a + off, pol);
         if (two) bv[c] = ld16_stream<T>(pc.b + off, pol);
       }
+      if constexpr (KIND == 2) {
+        T xa[FCH][VN], xb[FCH][VN];
+#pragma unroll
+        for (int c = 0; c < FCH; ++c)
+#pragma unroll
+          for (int e = 0; e < VN; ++e) {
+            xa[c][e] = av[c].v[e];
+            xb[c][e] = two ? bv[c].v[e] : T(0);
+          }
+        ve.template eval_all<FCH * VN>(&xa[0][0], &xb[0][0]);
+#pragma unroll
+        for (int c = 0; c < FCH; ++c)
+#pragma unroll
+          for (int e = 0; e < VN; ++e) av[c].v[e] = xa[c][e];
+      }
 #pragma unroll
       for (int c = 0; c < FCH; ++c) {
         const int64_t off = (base + (int64_t)(c * FT + tid) * VN) * (int64_t)sizeof(T);
         V16<T> o;
 #pragma unroll
-        for (int e = 0; e < VN; ++e) o.v[e] = tr_eval<T, KIND>(ve, av[c].v[e], two ? bv[c].v[e] : T(0));
+        for (int e = 0; e < VN; ++e)
+          o.v[e] = KIND == 2 ? av[c].v[e] : tr_eval<T, KIND>(ve, av[c].v[e], two ? bv[c].v[e] : T(0));
         st16_hint<T>(pc.o + off, o, pol);
       }
     } else {

@@ -88,14 +88,29 @@ __global__ void __launch_bounds__(RT, RCTAS) k_reduce(const __grid_constant__ Re
         for (int c = 0; c < RCH; ++c)
           rb[c] = ld16<T>(pc.b + (base + (int64_t)(c * RT + tid) * V) * (int64_t)sizeof(T));
       }
+      if constexpr (KIND == 2) {
+        T xa[RCH][V], xb[RCH][V];
 #pragma unroll
-      for (int c = 0; c < RCH; ++c)
+        for (int c = 0; c < RCH; ++c)
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-          if constexpr (KIND == 0) acc[e] = O::apply(acc[e], ra[c].v[e]);
-          else if constexpr (KIND == 1) acc[e] = mul_add(ra[c].v[e], rb[c].v[e], acc[e]);
-          else acc[e] = O::apply(acc[e], ve(ra[c].v[e], two ? rb[c].v[e] : T(0)));
-        }
+          for (int e = 0; e < V; ++e) {
+            xa[c][e] = ra[c].v[e];
+            xb[c][e] = two ? rb[c].v[e] : T(0);
+          }
+        ve.template eval_all<RCH * V>(&xa[0][0], &xb[0][0]);
+#pragma unroll
+        for (int c = 0; c < RCH; ++c)
+#pragma unroll
+          for (int e = 0; e < V; ++e) acc[e] = O::apply(acc[e], xa[c][e]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < RCH; ++c)
+#pragma unroll
+          for (int e = 0; e < V; ++e) {
+            if constexpr (KIND == 0) acc[e] = O::apply(acc[e], ra[c].v[e]);
+            else acc[e] = mul_add(ra[c].v[e], rb[c].v[e], acc[e]);
+          }
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < RCH; ++c)
@@ -147,13 +162,12 @@ cudaError_t go(const ReduceParams& p, int grid, cudaStream_t s) {
 template <typename T>
 cudaError_t dispatch(const ReduceParams& p, int grid, cudaStream_t s) {
   const int kind = p.vc.kind;
-  if (p.op == DR_PLUS && kind == 0) return go<T, DR_PLUS, 0>(p, grid, s);
   if (p.op == DR_PLUS && kind == 1) return go<T, DR_PLUS, 1>(p, grid, s);
   switch (p.op) {
-    case DR_PLUS: return go<T, DR_PLUS, 2>(p, grid, s);
-    case DR_MUL: return go<T, DR_MUL, 2>(p, grid, s);
-    case DR_MIN: return go<T, DR_MIN, 2>(p, grid, s);
-    default: return go<T, DR_MAX, 2>(p, grid, s);
+    case DR_PLUS: return kind == 0 ? go<T, DR_PLUS, 0>(p, grid, s) : go<T, DR_PLUS, 2>(p, grid, s);
+    case DR_MUL: return kind == 0 ? go<T, DR_MUL, 0>(p, grid, s) : go<T, DR_MUL, 2>(p, grid, s);
+    case DR_MIN: return kind == 0 ? go<T, DR_MIN, 0>(p, grid, s) : go<T, DR_MIN, 2>(p, grid, s);
+    default: return kind == 0 ? go<T, DR_MAX, 0>(p, grid, s) : go<T, DR_MAX, 2>(p, grid, s);
   }
 }
 

@@ -132,12 +132,15 @@ __device__ __forceinline__ void tile_values(const TileRef& r, bool two, int tid,
   constexpr int V = 16 / sizeof(T);
   if (r.full) {
 #pragma unroll
-    for (int c = 0; c < SCH; ++c)
+    for (int c = 0; c < SCH; ++c) {
+      T y[V];
 #pragma unroll
       for (int e = 0; e < V; ++e) {
-        if constexpr (KIND == 0) x[c][e] = xa[c].v[e];
-        else x[c][e] = ve(xa[c].v[e], two ? xb[c].v[e] : T(0));
+        x[c][e] = xa[c].v[e];
+        y[e] = two ? xb[c].v[e] : T(0);
       }
+      if constexpr (KIND != 0) ve.template eval_all<V>(&x[c][0], y);
+    }
   } else {
 #pragma unroll
     for (int c = 0; c < SCH; ++c)
@@ -223,11 +226,11 @@ __device__ __forceinline__ void stage_issue(const ScanParams& P, long long lt, c
   mbar_arrive(bar);
 }
 
-// KIND: 0 = one leaf, no ops (PLUS only); 2 = generic fused view.
+// KIND: 0 = one leaf, no ops; 2 = generic fused view.
 // REV: scan from the last element to the first (reverse inclusive scan).
 // EXCL: exclusive scan with init.
 template <typename T, int OP, int KIND, bool REV, bool EXCL>
-__global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
+__global__ void __launch_bounds__(ST, KIND == 2 ? 2 : kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
   constexpr int V = 16 / sizeof(T);
   using O = Op<OP>;
   extern __shared__ __align__(128) char s_stage[];  // kStages x kTileBytes
@@ -286,11 +289,13 @@ __global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__
             va = *reinterpret_cast<const V16<T>*>(sp);
           V16<T> vb;
           if (two) vb = ld16_hint<T>(rr.pc->b + (rr.base + (int64_t)(c * ST + tid) * V) * (int64_t)sizeof(T), keep);
+          T y[V];
 #pragma unroll
           for (int e = 0; e < V; ++e) {
-            if constexpr (KIND == 0) x[c][e] = va.v[e];
-            else x[c][e] = ve(va.v[e], two ? vb.v[e] : T(0));
+            x[c][e] = va.v[e];
+            y[e] = two ? vb.v[e] : T(0);
           }
+          if constexpr (KIND != 0) ve.template eval_all<V>(&x[c][0], y);
         }
       } else {
         V16<T> na[SCH], nb[SCH];
@@ -423,8 +428,12 @@ cudaError_t go(const ScanParams& p, int grid, cudaStream_t s) {
 
 template <typename T, int OP>
 cudaError_t dispatch_op(const ScanParams& p, int grid, cudaStream_t s) {
-  if (p.exclusive) return go<T, OP, 2, false, true>(p, grid, s);
-  if (OP == DR_PLUS && p.vc.kind == 0) return go<T, DR_PLUS, 0, false, false>(p, grid, s);
+  // KIND 0 (a plain vector) for every operator; the interpreted view otherwise
+  if (p.exclusive) {
+    if (p.vc.kind == 0) return go<T, OP, 0, false, true>(p, grid, s);
+    return go<T, OP, 2, false, true>(p, grid, s);
+  }
+  if (p.vc.kind == 0) return go<T, OP, 0, false, false>(p, grid, s);
   return go<T, OP, 2, false, false>(p, grid, s);
 }
 

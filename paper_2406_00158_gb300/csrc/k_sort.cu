@@ -179,10 +179,23 @@ __device__ __forceinline__ int load_tile(const SortParams& P, int64_t tile, type
     ViewEval<T> ve;
     ve.init(P.vc);
     const bool two = P.vc.nleaf == 2;
+    if (SRC == 1 && cnt == STILE) {
+      T xa[SIT], xb[SIT];
 #pragma unroll
-    for (int i = 0; i < SIT; ++i) {
-      const int pos = w * 32 * SIT + i * 32 + lane;
-      key[i] = pos < cnt ? KO::to(view_elem<T, SRC>(pc, base + pos, ve, two)) : K(0);
+      for (int i = 0; i < SIT; ++i) {
+        const int64_t j = base + w * 32 * SIT + i * 32 + lane;
+        xa[i] = reinterpret_cast<const T*>(pc.a)[j];
+        xb[i] = two ? reinterpret_cast<const T*>(pc.b)[j] : T(0);
+      }
+      ve.template eval_all<SIT>(xa, xb);
+#pragma unroll
+      for (int i = 0; i < SIT; ++i) key[i] = KO::to(xa[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < SIT; ++i) {
+        const int pos = w * 32 * SIT + i * 32 + lane;
+        key[i] = pos < cnt ? KO::to(view_elem<T, SRC>(pc, base + pos, ve, two)) : K(0);
+      }
     }
   }
   return cnt;
@@ -257,6 +270,10 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const __grid_constant__ Sor
   __shared__ int dshift[RADIX];  // global start of digit d here minus its tile start
   __shared__ unsigned wsum[SW];
   __shared__ int64_t ostart[DST == 1 ? kMaxPieces : 1];
+  // last pass: per digit run, the output segment holding its first key, as the
+  // address of global index 0 in that segment's frame and the segment's end
+  __shared__ unsigned long long dbase[DST == 1 ? RADIX : 1];
+  __shared__ unsigned dsegend[DST == 1 ? RADIX : 1];
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int shift = 8 * P.pass;
@@ -291,6 +308,16 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const __grid_constant__ Sor
   if (d < RADIX) {
     dstart[d] = ds;
     dshift[d] = (int)gstart - (int)ds;
+    if constexpr (DST == 1) {
+      int lo = 0, hi = P.npout - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ostart[mid] <= (int64_t)gstart) lo = mid;
+        else hi = mid - 1;
+      }
+      dbase[d] = (unsigned long long)P.out[lo].p - (unsigned long long)ostart[lo] * sizeof(T);
+      dsegend[d] = lo + 1 < P.npout ? (unsigned)ostart[lo + 1] : (unsigned)P.n;
+    }
   }
   __syncthreads();
 
@@ -309,6 +336,9 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const __grid_constant__ Sor
     if (g >= (unsigned)P.n) continue;  // only if the counts' scan gave up a wait
     if constexpr (DST == 0) {
       reinterpret_cast<K*>(P.dst)[g] = k;
+    } else if (g >= (unsigned)(dshift[dd] + (int)dstart[dd]) && g < dsegend[dd]) {
+      // the run's segment (a run crosses into the next segment only at a boundary)
+      *reinterpret_cast<T*>(dbase[dd] + (unsigned long long)g * sizeof(T)) = KO::from(k);
     } else {
       int lo = 0, hi = P.npout - 1;
       while (lo < hi) {
