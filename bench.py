@@ -330,6 +330,24 @@ def measure_rows(api, dev, s, peak) -> dict:
                                        note="GB/s over 136 B/key (histogram + 8 passes of 16 B)")
     del vin, vout, xi
 
+    # fused views (Sec. 4.4): the view is evaluated in the kernel's loads, no intermediate
+    # array; 2^26 fp32 in 8 segments, bytes = what the fused kernel must move
+    m = 1 << 26
+    fx = api.SegmentedVector.from_tensor(torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_DOT_X, m)).to(dev), [m // 8] * 8)
+    fy = api.SegmentedVector.from_tensor(torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_DOT_Y, m)).to(dev), [m // 8] * 8)
+    fo = api.SegmentedVector.empty([m // 8] * 8, torch.float32, dev)
+    fr = torch.zeros(1, dtype=torch.float32, device=dev)
+    chain = fx.view().transform("scale", 2.0).transform("add", 1.0).transform("abs")
+    dv = api.dot_view(fx, fy)
+    for name, fn, nb in [("view_scan_zip*mul_f32_2^26", lambda: api.inclusive_scan(dv, fo, stream=s), 12),
+                         ("view_reduce_chain3_f32_2^26", lambda: api.transform_reduce(chain, fr, stream=s), 4),
+                         ("view_transform_chain3_f32_2^26", lambda: api.transform(chain, fo, stream=s), 8),
+                         ("view_scan_min_f32_2^26", lambda: api.inclusive_scan(fx, fo, op="min", stream=s), 8)]:
+        ms = _time(fn, s, 20, flush=lambda: flushbuf.zero_())
+        rows[name] = _row(ms, nb * m, peak, l2="flushed between calls")
+    api.sync_status(s)
+    del fx, fy, fo, chain, dv
+
     # autograd: scan n = 2^26 in 8 segments, fwd + bwd (reverse scan)
     n = 1 << 26
     xs = [q.clone().requires_grad_(True) for q in
