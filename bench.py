@@ -339,7 +339,8 @@ def measure_rows(api, dev, s, peak) -> dict:
     fr = torch.zeros(1, dtype=torch.float32, device=dev)
     chain = fx.view().transform("scale", 2.0).transform("add", 1.0).transform("abs")
     dv = api.dot_view(fx, fy)
-    for name, fn, nb in [("view_scan_zip*mul_f32_2^26", lambda: api.inclusive_scan(dv, fo, stream=s), 12),
+    for name, fn, nb in [("view_scan_plain_f32_2^26", lambda: api.inclusive_scan(fx, fo, stream=s), 8),
+                         ("view_scan_zip*mul_f32_2^26", lambda: api.inclusive_scan(dv, fo, stream=s), 12),
                          ("view_reduce_chain3_f32_2^26", lambda: api.transform_reduce(chain, fr, stream=s), 4),
                          ("view_transform_chain3_f32_2^26", lambda: api.transform(chain, fo, stream=s), 8),
                          ("view_scan_min_f32_2^26", lambda: api.inclusive_scan(fx, fo, op="min", stream=s), 8)]:
