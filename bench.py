@@ -409,6 +409,12 @@ def main() -> None:
     ap.add_argument("--log2n", type=int, default=28, help="headline size 2^log2n (profiling captures use less)")
     ap.add_argument("--stencil-only", type=int, default=0, metavar="N",
                     help="profiling helper: only run the stencil on an N x N grid (8 row blocks), 5 steps")
+    ap.add_argument("--scan-only", default="", metavar="DTYPE",
+                    help="profiling helper: only the inclusive scan of 2^log2n int64 (i64) or fp32 (f32) "
+                         "elements in 4 segments 1:2:3:2, 5 times")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="NVEC",
+                    help="profiling helper: only the batched scan + dot over NVEC vectors of the batch "
+                         "recipe, one launch, 5 times")
     ap.add_argument("--sort-only", action="store_true",
                     help="profiling helper: only sort 2^log2n fp32 keys in 8 segments, 5 times")
     ap.add_argument("--foreach-only", default="", metavar="FN",
@@ -426,6 +432,37 @@ def main() -> None:
     global N_ELEMS
     N_ELEMS = 1 << args.log2n
     build.build()
+    if args.scan_only:
+        n = N_ELEMS
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        lens = inputs.proportional_segments(n, [1, 2, 3, 2])
+        if args.scan_only == "i64":
+            x = torch.from_numpy(inputs.uniform_int64(inputs.SEED_SCAN_I64, n)).to(dev)
+        else:
+            x = torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_DOT_X, n)).to(dev)
+        vx = api.SegmentedVector.from_tensor(x, lens)
+        vo = api.SegmentedVector.empty(lens, x.dtype, dev)
+        v = vx.view()
+        s = torch.cuda.current_stream()
+        ms = _time(lambda: api.inclusive_scan(v, vo, stream=s), s, 5)
+        api.sync_status(s)
+        nb = 2 * x.element_size() * n
+        print(json.dumps({"scan": args.scan_only, "n": n, "ms": ms, "GB/s": nb / (ms / 1e3) / 1e9}))
+        return
+    if args.batched_only:
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        shapes = inputs.batch_shapes(inputs.SEED_BATCH, args.batched_only)
+        tot = sum(map(sum, shapes))
+        X = api.packed_vectors(inputs.uniform_pm1_f32(inputs.SEED_BATCH_X, tot), shapes, device=dev)
+        Pv = api.packed_vectors(inputs.uniform_pm1_f32(inputs.SEED_BATCH_P, tot), shapes, device=dev)
+        Y = api.packed_vectors(None, shapes, device=dev)
+        batch = api.Batch(X, Pv, Y, torch.zeros(len(shapes), dtype=torch.float32, device=dev))
+        s = torch.cuda.current_stream()
+        ms = _time(lambda: batch.run(stream=s), s, 5)
+        api.sync_status(s)
+        print(json.dumps({"batched": len(shapes), "elements": tot, "tune": list(batch.tune), "ms": ms,
+                          "GB/s": 12 * tot / (ms / 1e3) / 1e9}))
+        return
     if args.sort_only:
         n = N_ELEMS
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))

@@ -76,18 +76,50 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+namespace {
+// Per device: the library's stream-ordered memory pool (memory stays cached in
+// the pool: release threshold unbounded) and a stream on which frees are queued.
+struct DevPool {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t free_stream = nullptr;
+};
+DevPool* dev_pool(int dev) {
+  static std::mutex m;
+  static DevPool pools[64];
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(m);
+  DevPool& d = pools[dev];
+  if (!d.pool) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t thr = ~uint64_t(0);
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    cudaStream_t fs = nullptr;
+    if (cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      return nullptr;
+    }
+    d.pool = p;
+    d.free_stream = fs;
+  }
+  return &d;
+}
+}  // namespace
+
 int Workspace::ensure(size_t need, cudaStream_t s) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (ptr && bytes >= need && device == dev) return DR_OK;
-  if (ptr) {
-    // the old workspace may still be in use by work queued on `s`
-    cudaStreamSynchronize(s);
-    release();
-  }
+  if (ptr) release();  // behind its last use; the pool orders any reuse after the free
+  DevPool* dp = dev_pool(dev);
+  if (!dp) return fail(DR_E_CUDA, "workspace pool for device %d could not be created", dev);
   need = (need + 255) / 256 * 256;
-  e = cudaMalloc(&ptr, need);
+  e = cudaMallocFromPoolAsync(&ptr, need, dp->pool, s);
   if (e != cudaSuccess) {
     ptr = nullptr;
     return fail(DR_E_NOMEM, "workspace allocation of %zu bytes failed: %s", need, cudaGetErrorString(e));
@@ -96,7 +128,18 @@ int Workspace::ensure(size_t need, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
   bytes = need;
   device = dev;
+  marked = false;
   return DR_OK;
+}
+
+void Workspace::mark(cudaStream_t s) {
+  if (!ptr) return;
+  if (!last && cudaEventCreateWithFlags(&last, cudaEventDisableTiming) != cudaSuccess) {
+    last = nullptr;
+    marked = false;
+    return;
+  }
+  marked = cudaEventRecord(last, s) == cudaSuccess;
 }
 
 void Workspace::release() {
@@ -104,10 +147,18 @@ void Workspace::release() {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
-    cudaDeviceSynchronize();  // kernels queued on any stream may still use it
-    cudaFree(ptr);
+    DevPool* dp = dev_pool(device);
+    if (marked && dp) {
+      cudaStreamWaitEvent(dp->free_stream, last, 0);
+    } else {
+      cudaDeviceSynchronize();  // unknown last use: kernels on any stream may still use it
+    }
+    cudaFreeAsync(ptr, dp ? dp->free_stream : nullptr);
     if (cur != device) cudaSetDevice(cur);
   }
+  if (last) cudaEventDestroy(last);
+  last = nullptr;
+  marked = false;
   ptr = nullptr;
   bytes = 0;
   device = -1;
@@ -558,6 +609,7 @@ extern "C" int dr_view_destroy(dr_view* v) {
   if (v) {
     v->ws_scan.release();
     v->ws_reduce.release();
+    v->ws_sort.release();
   }
   delete v;
   return DR_OK;
@@ -657,6 +709,7 @@ static int do_scan(const char* who, const dr_view* in_c, dr_vec* out, int op, bo
   p.skip_tile = take_skip_publish();
   if (exclusive) std::memcpy(&p.init_bits, init, esize(in->dtype));
   cudaError_t e = launch_scan(p, reverse, scan_grid(in->dtype, p.ntiles), s);
+  in->ws_scan.mark(s);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
 }
 
@@ -695,6 +748,7 @@ extern "C" int dr_transform_reduce(const dr_view* in_c, int op, const void* init
   p.ws = static_cast<char*>(in->ws_reduce.ptr);
   p.status = status_word();
   cudaError_t e = launch_reduce(p, grid, s);
+  in->ws_reduce.mark(s);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
 }
 
@@ -884,6 +938,7 @@ extern "C" int dr_sort(const dr_view* in_c, dr_vec* out, dr_stream_t stream) {
   p.spin_limit = spin_limit();
   cudaError_t e = cudaSuccess;
   e = launch_sort(p, L, s);
+  in->ws_sort.mark(s);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
 }
 

@@ -23,13 +23,21 @@ int esize(int dtype);
 bool valid_dtype(int dtype);
 
 // Device workspace owned by a handle: allocated (and zeroed) on first use,
-// grown when a larger one is needed.  Kernels keep it self-cleaning.
+// grown when a larger one is needed.  Kernels keep it self-cleaning.  Memory
+// comes from a per-device pool of the library in stream order, so allocating
+// and releasing never synchronizes the device: mark(s) after the launches that
+// use it records an event, and release() frees the memory behind that event.
+// A workspace that was never marked is released after a device synchronization.
 struct Workspace {
   void* ptr = nullptr;
   size_t bytes = 0;
   int device = -1;
+  cudaEvent_t last = nullptr;  // recorded after the latest use (mark)
+  bool marked = false;
   int ensure(size_t need, cudaStream_t s);
+  void mark(cudaStream_t s);
   void release();
+  ~Workspace() { release(); }
 };
 
 unsigned* status_word();      // device address of the current device's status word
