@@ -415,6 +415,9 @@ def main() -> None:
     ap.add_argument("--batched-only", type=int, default=0, metavar="NVEC",
                     help="profiling helper: only the batched scan + dot over NVEC vectors of the batch "
                          "recipe, one launch, 5 times")
+    ap.add_argument("--link-only", action="store_true",
+                    help="measurement helper: host<->device copy bandwidth of 1 GiB pinned buffers "
+                         "(the link that bounds the end-to-end number)")
     ap.add_argument("--sort-only", action="store_true",
                     help="profiling helper: only sort 2^log2n fp32 keys in 8 segments, 5 times")
     ap.add_argument("--foreach-only", default="", metavar="FN",
@@ -432,6 +435,17 @@ def main() -> None:
     global N_ELEMS
     N_ELEMS = 1 << args.log2n
     build.build()
+    if args.link_only:
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        nb = 1 << 30
+        h = torch.empty(nb // 4, dtype=torch.float32).pin_memory()
+        d = torch.empty(nb // 4, dtype=torch.float32, device=dev)
+        s = torch.cuda.current_stream()
+        h2d = _time(lambda: d.copy_(h, non_blocking=True), s, 5)
+        d2h = _time(lambda: h.copy_(d, non_blocking=True), s, 5)
+        print(json.dumps({"link": "pinned host <-> HBM, 1 GiB, cudaMemcpyAsync",
+                          "h2d_GB/s": nb / (h2d / 1e3) / 1e9, "d2h_GB/s": nb / (d2h / 1e3) / 1e9}))
+        return
     if args.scan_only:
         n = N_ELEMS
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
