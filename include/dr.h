@@ -25,6 +25,8 @@
  *     per-device status word that dr_sync_status() reads and clears.
  *   - A handle that carries device workspace (views passed to algorithms,
  *     batch plans) must not be used by two calls that can overlap on the GPU.
+ *     A view's workspace is freed, when the view is destroyed, in the order of
+ *     the stream its latest call used: destroy a view before that stream.
  *   - Element types: fp32, fp64, int64, int32.  Integer arithmetic wraps mod
  *     2^bits; floating-point arithmetic is IEEE round-to-nearest, no fast-math.
  */

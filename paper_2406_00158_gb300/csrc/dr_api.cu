@@ -78,7 +78,8 @@ int sm_count() {
 
 namespace {
 // Per device: the library's stream-ordered memory pool (memory stays cached in
-// the pool: release threshold unbounded) and a stream on which frees are queued.
+// the pool: release threshold unbounded) and a stream for frees of workspaces
+// whose last use is unknown.
 struct DevPool {
   cudaMemPool_t pool = nullptr;
   cudaStream_t free_stream = nullptr;
@@ -134,12 +135,8 @@ int Workspace::ensure(size_t need, cudaStream_t s) {
 
 void Workspace::mark(cudaStream_t s) {
   if (!ptr) return;
-  if (!last && cudaEventCreateWithFlags(&last, cudaEventDisableTiming) != cudaSuccess) {
-    last = nullptr;
-    marked = false;
-    return;
-  }
-  marked = cudaEventRecord(last, s) == cudaSuccess;
+  last = s;
+  marked = true;
 }
 
 void Workspace::release() {
@@ -147,16 +144,15 @@ void Workspace::release() {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != device) cudaSetDevice(device);
-    DevPool* dp = dev_pool(device);
-    if (marked && dp) {
-      cudaStreamWaitEvent(dp->free_stream, last, 0);
+    if (marked) {
+      cudaFreeAsync(ptr, last);  // after the work queued on the stream of the last use
     } else {
-      cudaDeviceSynchronize();  // unknown last use: kernels on any stream may still use it
+      cudaDeviceSynchronize();   // unknown last use: kernels on any stream may still use it
+      DevPool* dp = dev_pool(device);
+      cudaFreeAsync(ptr, dp ? dp->free_stream : nullptr);
     }
-    cudaFreeAsync(ptr, dp ? dp->free_stream : nullptr);
     if (cur != device) cudaSetDevice(cur);
   }
-  if (last) cudaEventDestroy(last);
   last = nullptr;
   marked = false;
   ptr = nullptr;

@@ -26,13 +26,15 @@ bool valid_dtype(int dtype);
 // grown when a larger one is needed.  Kernels keep it self-cleaning.  Memory
 // comes from a per-device pool of the library in stream order, so allocating
 // and releasing never synchronizes the device: mark(s) after the launches that
-// use it records an event, and release() frees the memory behind that event.
-// A workspace that was never marked is released after a device synchronization.
+// use it remembers the stream, and release() frees the memory on that stream,
+// after the work queued there (the next allocation on the same stream reuses it
+// at once).  A workspace that was never marked is released after a device
+// synchronization.
 struct Workspace {
   void* ptr = nullptr;
   size_t bytes = 0;
   int device = -1;
-  cudaEvent_t last = nullptr;  // recorded after the latest use (mark)
+  cudaStream_t last = nullptr;  // stream of the latest use (mark)
   bool marked = false;
   int ensure(size_t need, cudaStream_t s);
   void mark(cudaStream_t s);

@@ -219,3 +219,57 @@ def test_bounded_wait_reports_timeout_and_recovers(api):
     api.inclusive_scan(vx, out)
     api.sync_status()
     assert np.array_equal(G.to_np(out), oracle.inclusive_scan_i64(x))
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+@pytest.mark.parametrize("dt", [np.int32, np.float64])
+def test_exclusive_scan_max_min_plain_and_viewed(api, op, dt):
+    """Exclusive MIN / MAX scans (plain vectors take the un-interpreted kernel) and an
+    exclusive PLUS scan over a transformed view (the interpreted one), several tiles
+    and a ragged tail, against the definition."""
+    n = 3 * 8192 + 77
+    x = inputs.uniform_int64(63, n, -500, 500).astype(dt)
+    lens = [5, n - 10, 5]
+    tdt = torch.int32 if dt == np.int32 else torch.float64
+    out = G.empty_like_vec(lens, tdt)
+    init = 3
+    api.exclusive_scan(G.segvec(x, lens), out, init=init, op=op)
+    api.sync_status()
+    f = np.maximum if op == "max" else np.minimum
+    exp = np.empty(n, dt)
+    acc = dt(init)
+    for i in range(n):          # the definition: out_i = init op x_0 op ... op x_{i-1}
+        exp[i] = acc
+        acc = f(acc, x[i])
+    assert np.array_equal(G.to_np(out), exp)
+    # exclusive PLUS over view = transform(x, scale 2) | add 1
+    v = G.segvec(x, lens).view().transform("scale", 2).transform("add", 1)
+    api.exclusive_scan(v, out, init=0)
+    api.sync_status()
+    y = (2 * x.astype(np.int64) + 1) if dt == np.int32 else (2 * x + 1)
+    cs = np.concatenate([[0], np.cumsum(y)[:-1]])
+    if dt == np.int32:
+        assert np.array_equal(G.to_np(out).astype(np.int64), cs.astype(np.int32).astype(np.int64))
+    else:
+        assert np.array_equal(G.to_np(out), cs)   # small integers in fp64: exact
+
+
+def test_scan_over_zip_view_float_within_bound(api):
+    """inclusive_scan(zip(x, y) | multiply) in fp32 through the interpreted view path:
+    within the scan bound of the FP64 prefix of x_i * y_i."""
+    from tests import tolerances as T
+    n = 5 * 8192 + 3
+    x = inputs.uniform_pm1_f32(65, n)
+    y = inputs.uniform_pm1_f32(66, n)
+    lens_x, lens_y = [4000, n - 4000], [n // 3, n - n // 3]
+    out = G.empty_like_vec([n], torch.float32)
+    api.inclusive_scan(api.dot_view(G.segvec(x, lens_x), G.segvec(y, lens_y)), out)
+    api.sync_status()
+    prod = x.astype(np.float64) * y.astype(np.float64)   # exact products of fp32 values
+    ref = oracle.inclusive_scan_f64(prod)
+    absref = oracle.inclusive_scan_f64(np.abs(prod))
+    pieces = [4000, n // 3 - 4000, n - n // 3]
+    tiles = G.tile_index(pieces, 8192)
+    # each product is rounded once to fp32 before the scan: one more rounding per term
+    bound = T.scan_bound(absref, tiles) + 2.0 ** -24 * absref
+    assert np.all(np.abs(G.to_np(out).astype(np.float64) - ref) <= bound)
