@@ -212,25 +212,30 @@ __device__ __forceinline__ T block_totals(const T* s_tot, int lane, T (&loc)[SR]
 // tile, completing on the stage's mbarrier), or completes the barrier's phase
 // without a copy (ragged tile, or no tile).  One arrival per call either way, so
 // a stage's barrier phase counts its uses.
+// With two leaves (a zip view), the tile's range of leaf b is prefetched into
+// L2 at the same time, so the R phase's loads of b hit L2.
 template <typename T, bool REV>
 __device__ __forceinline__ void stage_issue(const ScanParams& P, long long lt, char* stage,
-                                            unsigned long long* bar) {
+                                            unsigned long long* bar, bool two = false) {
   if (lt < P.ntiles) {
     const TileRef r = tile_ref<T, REV>(P, lt);
     if (r.full) {
       mbar_expect_tx(bar, kTileBytes);
       bulk_g2s(stage, r.pc->a + r.base * (int64_t)sizeof(T), kTileBytes, bar);
+      if (two) bulk_prefetch_l2(r.pc->b + r.base * (int64_t)sizeof(T), kTileBytes);
       return;
     }
   }
   mbar_arrive(bar);
 }
 
-// KIND: 0 = one leaf, no ops; 2 = generic fused view.
+// KIND: 0 = one leaf, no ops; 2 = generic fused view of one leaf; 3 = generic
+// fused view of two leaves (a zip; the only one that needs the second tile's
+// registers, so the one-leaf view keeps the plain kernel's occupancy).
 // REV: scan from the last element to the first (reverse inclusive scan).
 // EXCL: exclusive scan with init.
 template <typename T, int OP, int KIND, bool REV, bool EXCL>
-__global__ void __launch_bounds__(ST, KIND == 2 ? 2 : kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
+__global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
   constexpr int V = 16 / sizeof(T);
   using O = Op<OP>;
   extern __shared__ __align__(128) char s_stage[];  // kStages x kTileBytes
@@ -245,8 +250,8 @@ __global__ void __launch_bounds__(ST, KIND == 2 ? 2 : kMinBlocks) k_scan(const _
   const unsigned tag = (ld_relaxed_u32(&hdr->epoch) & 0x3fffffffu) << 2;
 
   ViewEval<T> ve;
-  if constexpr (KIND == 2) ve.init(P.vc);
-  const bool two = KIND == 2 && P.vc.nleaf == 2;
+  if constexpr (KIND >= 2) ve.init(P.vc);
+  const bool two = KIND == 3 && P.vc.nleaf == 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T ident = O::template identity<T>();
   const unsigned long long keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(ST, KIND == 2 ? 2 : kMinBlocks) k_scan(const _
     fence_mbar_init();
     for (int d = 0; d < kStages; ++d) {
       s_tk[d] = (long long)atomicAdd(&hdr->ticket, 1ull);
-      stage_issue<T, REV>(P, s_tk[d], s_stage + d * kTileBytes, &s_bar[d]);
+      stage_issue<T, REV>(P, s_tk[d], s_stage + d * kTileBytes, &s_bar[d], two);
     }
   }
   __syncthreads();
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__(ST, KIND == 2 ? 2 : kMinBlocks) k_scan(const _
     const long long tn = tlast < P.ntiles ? s_tk[kStages] : P.ntiles;
     if (tid == 0) {
       fence_proxy_async_smem();
-      stage_issue<T, REV>(P, tn, s_stage + sidx * kTileBytes, &s_bar[sidx]);
+      stage_issue<T, REV>(P, tn, s_stage + sidx * kTileBytes, &s_bar[sidx], two);
     }
     parity ^= 1u << sidx;
     if (warp == 0) aggprev = s_agg;
@@ -429,19 +434,20 @@ cudaError_t go(const ScanParams& p, int grid, cudaStream_t s) {
 template <typename T, int OP>
 cudaError_t dispatch_op(const ScanParams& p, int grid, cudaStream_t s) {
   // KIND 0 (a plain vector) for every operator; the interpreted view otherwise
+  const bool zip = p.vc.nleaf == 2;
   if (p.exclusive) {
     if (p.vc.kind == 0) return go<T, OP, 0, false, true>(p, grid, s);
-    return go<T, OP, 2, false, true>(p, grid, s);
+    return zip ? go<T, OP, 3, false, true>(p, grid, s) : go<T, OP, 2, false, true>(p, grid, s);
   }
   if (p.vc.kind == 0) return go<T, OP, 0, false, false>(p, grid, s);
-  return go<T, OP, 2, false, false>(p, grid, s);
+  return zip ? go<T, OP, 3, false, false>(p, grid, s) : go<T, OP, 2, false, false>(p, grid, s);
 }
 
 template <typename T>
 cudaError_t dispatch(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
   if (reverse) {
     if (p.vc.kind == 0) return go<T, DR_PLUS, 0, true, false>(p, grid, s);
-    return go<T, DR_PLUS, 2, true, false>(p, grid, s);
+    return p.vc.nleaf == 2 ? go<T, DR_PLUS, 3, true, false>(p, grid, s) : go<T, DR_PLUS, 2, true, false>(p, grid, s);
   }
   switch (p.op) {
     case DR_PLUS: return dispatch_op<T, DR_PLUS>(p, grid, s);
