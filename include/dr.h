@@ -7,9 +7,12 @@
  * concatenated in order form the whole range.  Here every memory locale is a
  * separate allocation in one GPU's HBM, so a segment is just (device pointer,
  * length).  Containers are built over caller-given segments, *views* are
- * composed lazily (Sec. 4.4: transform, zip) and algorithms (Sec. 4.3:
- * inclusive_scan, reduce / transform_reduce, for_each) run over a composition
- * with the view fused into the kernel's loads and stores.
+ * composed lazily (Sec. 4.4: transform, zip of two or k ranges, take / drop)
+ * and algorithms (Sec. 4.3: inclusive / exclusive scan, reduce /
+ * transform_reduce, for_each, transform, sort; and the 5-point stencil over a
+ * row-block array) run over a composition with the view fused into the
+ * kernel's loads and stores.  Adjoints (reverse scan, scale-by-partner,
+ * transposed stencil) and a batched persistent launch complete the set.
  *
  * Conventions for every entry point:
  *   - Returns an int status (enum dr_status); never throws or aborts across
