@@ -626,8 +626,10 @@ def main() -> None:
     if D.rank == 0 and D.world == 1 and not args.no_cpu_baseline:
         sample = 1 << 26
         dt, nb = cpu_oracle_run(x[:sample], y[:sample], 2)
+        import platform
         cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle FP64 dot + FP64 inclusive_scan over the first 2^26 elements, 2 repetitions"}
+               "sample": "oracle FP64 dot + FP64 inclusive_scan over the first 2^26 elements, 2 repetitions",
+               "host": {"machine": platform.machine(), "logical_cpus": os.cpu_count()}}
 
     rows = {}
     if not args.no_rows:
@@ -647,6 +649,9 @@ def main() -> None:
                      "per_kernel": {k: {"ms": v[0], "GB/s": v[1] / (v[0] / 1e3) / 1e9,
                                         "frac": v[1] / (v[0] / 1e3) / 1e9 / peak} for k, v in kern.items()}},
         "clocks": clk,
+        "device": {"name": torch.cuda.get_device_name(dev),
+                   "sms": torch.cuda.get_device_properties(dev).multi_processor_count,
+                   "l2_bytes": torch.cuda.get_device_properties(dev).L2_cache_size},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 2 * N_ELEMS * 4,
                 "d2h_bytes_per_step": N_ELEMS * 4 + 4} if e2e_val is not None else None,
         "gpu_launches": 2 * K,
