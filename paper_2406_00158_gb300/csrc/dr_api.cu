@@ -111,7 +111,7 @@ DevPool* dev_pool(int dev) {
 }
 }  // namespace
 
-int Workspace::ensure(size_t need, cudaStream_t s) {
+int Workspace::ensure(size_t need, cudaStream_t s, size_t zero) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -125,7 +125,7 @@ int Workspace::ensure(size_t need, cudaStream_t s) {
     ptr = nullptr;
     return fail(DR_E_NOMEM, "workspace allocation of %zu bytes failed: %s", need, cudaGetErrorString(e));
   }
-  e = cudaMemsetAsync(ptr, 0, need, s);
+  e = cudaMemsetAsync(ptr, 0, zero < need ? zero : need, s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(workspace)");
   bytes = need;
   device = dev;
@@ -921,7 +921,7 @@ extern "C" int dr_sort(const dr_view* in_c, dr_vec* out, dr_stream_t stream) {
   const size_t counts_b = up((size_t)ncounts * 4), tmp_b = up((size_t)n * esz);
   // the scan's workspace comes first so that it keeps its (self-cleaning) state when
   // the workspace is reused; it is zeroed once, when allocated
-  if (int r = in->ws_sort.ensure(scan_b + counts_b + 2 * tmp_b, s)) return r;
+  if (int r = in->ws_sort.ensure(scan_b + counts_b + 2 * tmp_b, s, scan_b)) return r;
   char* ws = static_cast<char*>(in->ws_sort.ptr);
   L.scan_ws = ws;
   p.counts = reinterpret_cast<unsigned*>(ws + scan_b);

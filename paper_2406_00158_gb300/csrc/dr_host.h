@@ -36,7 +36,9 @@ struct Workspace {
   int device = -1;
   cudaStream_t last = nullptr;  // stream of the latest use (mark)
   bool marked = false;
-  int ensure(size_t need, cudaStream_t s);
+  // zero: bytes at the start that must read as zero before the first kernel
+  // (the self-cleaning counters); the rest is scratch the kernels write first
+  int ensure(size_t need, cudaStream_t s, size_t zero = ~size_t(0));
   void mark(cudaStream_t s);
   void release();
   ~Workspace() { release(); }
