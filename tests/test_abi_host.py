@@ -332,3 +332,23 @@ def test_more_than_128_pieces_is_unsupported_before_any_launch(lib):
     assert lib.dr_view_zipn(2, (ctypes.c_void_p * 2)(v, view_of(o)), ctypes.byref(z)) == 0
     assert lib.dr_for_each(z, 0, None, 0, None) == L.DR_E_UNSUPPORTED
     assert b"128" in L.lib().dr_last_error()
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU fallback: every entry point raises when the CUDA library is absent
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2406_00158_gb300 import _lib as L\n"
+        "L.LIB_PATH = %r\n"
+        "from paper_2406_00158_gb300 import api\n"
+        "try:\n"
+        "    api.block_lengths(10, 3)\n"
+        "except RuntimeError as e:\n"
+        "    print('raised:', e)\n"
+        "    sys.exit(0)\n"
+        "sys.exit(1)\n" % (ROOT, str(tmp_path / "absent.so")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "no CPU fallback" in r.stdout
