@@ -561,3 +561,26 @@ def test_partition_sort_equals_plain_sort(trial):
     x = inputs.uniform_int64(600 + trial, n, -span, span)
     assert np.array_equal(oracle.partition_sort_i64(lens, x), np.sort(x))
     assert np.array_equal(oracle.partition_sort_i64(lens, np.full(n, 5, np.int64)), np.full(n, 5))
+
+
+def test_black_scholes_fp32_bound_holds_for_a_plain_fp32_evaluation():
+    # the stated tolerance covers an ordinary fp32 evaluation (float32 log / exp /
+    # erfc, separately rounded ops) and is not vacuous: prices resolve to ~1e-6
+    from scipy.special import erfc
+    from tests import tolerances as T
+    S, X, Tm = inputs.black_scholes_inputs(1 << 15, key=RNG_KEY)
+    r = float(np.float32(inputs.BS_R))
+    sig = float(np.float32(inputs.BS_SIGMA))
+    f = np.float32
+    sv = f(sig) * np.sqrt(Tm)
+    d1 = (np.log(S / X) + (f(r) + f(0.5) * f(sig) * f(sig)) * Tm) / sv
+    d2 = d1 - sv
+    K = X * np.exp(-f(r) * Tm)
+    N = lambda d: (f(0.5) * erfc(-d * f(0.7071067811865476))).astype(np.float32)
+    call = S * N(d1) - K * N(d2)
+    put = K * N(-d2) - S * N(-d1)
+    assert call.dtype == np.float32 and put.dtype == np.float32
+    ec, ep, aux = oracle.black_scholes_f64(S, X, Tm, r, sig, aux=True)
+    bound = T.black_scholes_bound(S, X, Tm, r, sig, aux)
+    assert np.all(np.abs(call - ec) <= bound) and np.all(np.abs(put - ep) <= bound)
+    assert np.median(bound / (S + aux[:, 3])) < 2e-5
