@@ -44,7 +44,12 @@ template <int KB>
 struct Tile {
   static constexpr int IT = KB == 4 ? DR_SORT_ITEMS : DR_SORT_ITEMS / 2;
   static constexpr int N = ST * IT;
+  // the scatter kernel's static shared memory: staged keys, per-warp digit counts,
+  // per-digit starts / shifts / bases, output starts (must stay within 48 KB)
+  static constexpr int kSmem = N * KB + (ST / 32) * 256 * 4 + 256 * (4 + 4 + 8 + 4) + 128 * 8 + 64;
+  static_assert(kSmem <= 48 * 1024, "sort tile too large for static shared memory");
 };
+static_assert(Tile<4>::kSmem > 0 && Tile<8>::kSmem > 0, "tile shapes");
 
 // Order-preserving maps between element values and unsigned keys.
 template <typename T>
