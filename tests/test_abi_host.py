@@ -352,3 +352,30 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "no CPU fallback" in r.stdout
+
+
+def test_batch_plan_validation(lib):
+    # every rejection happens on the host, before the plan uploads anything
+    P = ctypes.c_void_p
+    arr = lambda *v: (P * len(v))(*v)
+    _, a = make_vec([100])
+    _, b = make_vec([100], ptrs=[1 << 41])
+    _, c = make_vec([100], ptrs=[1 << 42])
+    _, d64 = make_vec([100], dtype=L.DR_F64, ptrs=[1 << 43])
+    _, short = make_vec([99], ptrs=[1 << 44])
+    dots = P(1 << 45)
+    h = P()
+    assert lib.dr_batch_plan(0, arr(a), arr(b), arr(c), dots, None, ctypes.byref(h)) == L.DR_E_INVAL
+    assert lib.dr_batch_plan(1, arr(a), arr(b), arr(c), None, None, ctypes.byref(h)) == L.DR_E_INVAL
+    assert lib.dr_batch_plan(1, arr(a), arr(b), arr(c), P((1 << 45) + 2), None, ctypes.byref(h)) == L.DR_E_ALIGN
+    bad = L.dr_tune(100, 16, 3, 0)                          # 100 threads: not a supported shape
+    assert lib.dr_batch_plan(1, arr(a), arr(b), arr(c), dots, ctypes.byref(bad), ctypes.byref(h)) == L.DR_E_INVAL
+    assert lib.dr_batch_plan(1, arr(a), arr(d64), arr(c), dots, None, ctypes.byref(h)) == L.DR_E_DTYPE
+    assert lib.dr_batch_plan(1, arr(a), arr(short), arr(c), dots, None, ctypes.byref(h)) == L.DR_E_INVAL
+    assert lib.dr_batch_plan(2, arr(a, None), arr(b, b), arr(c, c), dots, None, ctypes.byref(h)) == L.DR_E_INVAL
+    many = [2] * 129                                        # one vector spanning 129 pieces
+    _, m = make_vec(many, ptrs=fake_ptrs(many, base=1 << 46))
+    _, mp = make_vec(many, ptrs=fake_ptrs(many, base=1 << 47))
+    _, my = make_vec([sum(many)], ptrs=[1 << 44])
+    assert lib.dr_batch_plan(1, arr(m), arr(mp), arr(my), dots, None, ctypes.byref(h)) == L.DR_E_UNSUPPORTED
+    assert not h.value
