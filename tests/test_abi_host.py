@@ -379,3 +379,28 @@ def test_batch_plan_validation(lib):
     _, my = make_vec([sum(many)], ptrs=[1 << 44])
     assert lib.dr_batch_plan(1, arr(m), arr(mp), arr(my), dots, None, ctypes.byref(h)) == L.DR_E_UNSUPPORTED
     assert not h.value
+
+
+def test_stencil_validation(lib):
+    # rejected on the host, before the halo exchange launches anything
+    def md2(base, rows=(3, 4), cols=16):
+        h = ctypes.c_void_p()
+        r = (ctypes.c_int64 * len(rows))(*rows)
+        p = (ctypes.c_void_p * len(rows))(*[base + (k << 28) for k in range(len(rows))])
+        assert lib.dr_md2_create(L.DR_F32, sum(rows), cols, len(rows), r, p, ctypes.byref(h)) == 0
+        return h
+    a, b, t = md2(1 << 36), md2(1 << 37), md2(1 << 38)
+    other = md2(1 << 39, rows=(4, 3))
+    wide = md2(1 << 40, cols=32)
+    S = lib.dr_stencil5
+    assert S(None, b, t, 1, 0.0, 0.25, None) == L.DR_E_INVAL
+    assert S(a, b, t, 0, 0.0, 0.25, None) == L.DR_E_INVAL          # steps >= 1
+    assert S(a, b, None, 2, 0.0, 0.25, None) == L.DR_E_INVAL       # tmp needed for > 1 step
+    assert S(a, other, t, 1, 0.0, 0.25, None) == L.DR_E_INVAL      # different blocking
+    assert S(a, wide, t, 1, 0.0, 0.25, None) == L.DR_E_INVAL       # different shape
+    assert S(a, a, t, 1, 0.0, 0.25, None) == L.DR_E_INVAL          # in == out
+    alias = md2(1 << 36)                                            # same storage as a
+    assert S(a, alias, t, 1, 0.0, 0.25, None) == L.DR_E_INVAL
+    assert lib.dr_stencil5_T(a, b, None, 3, 0.0, 0.25, None) == L.DR_E_INVAL
+    for h in (a, b, t, other, wide, alias):
+        lib.dr_md2_destroy(h)
