@@ -404,3 +404,23 @@ def test_stencil_validation(lib):
     assert lib.dr_stencil5_T(a, b, None, 3, 0.0, 0.25, None) == L.DR_E_INVAL
     for h in (a, b, t, other, wide, alias):
         lib.dr_md2_destroy(h)
+
+
+def test_scale_by_partner_validation(lib):
+    _, x = make_vec([64])
+    _, y = make_vec([64], ptrs=[1 << 41])
+    _, gx = make_vec([64], ptrs=[1 << 42])
+    _, g64 = make_vec([64], dtype=L.DR_F64, ptrs=[1 << 43])
+    _, gs = make_vec([63], ptrs=[1 << 44])
+    g = ctypes.c_void_p(1 << 45)
+    F = lib.dr_scale_by_partner
+    assert F(None, y, g, gx, None, None) == L.DR_E_INVAL
+    assert F(x, y, None, gx, None, None) == L.DR_E_INVAL
+    assert F(x, y, g, None, None, None) == L.DR_OK            # nothing requested: no launch
+    assert F(x, y, g, g64, None, None) == L.DR_E_DTYPE
+    assert F(x, y, g, gs, None, None) == L.DR_E_INVAL         # lengths differ
+    many = [1] * 129
+    _, mx = make_vec(many, ptrs=fake_ptrs(many, base=1 << 46))
+    _, my = make_vec([129], ptrs=[1 << 47])
+    _, mg = make_vec([129], ptrs=[1 << 40])
+    assert F(mx, my, g, mg, None, None) == L.DR_E_UNSUPPORTED
