@@ -372,23 +372,31 @@ extern "C" int dr_batch_autotune(dr_batch* b, int mode, const char* cache_path, 
   const int shapes[][4] = {{0, 128, 16, 8}, {0, 256, 8, 8}, {0, 256, 16, 8}, {0, 512, 8, 4},
                            {0, 512, 16, 4}, {1, 256, 16, 3}, {1, 256, 32, 1}};
   const int ctas[] = {1, 2, 3, 4, 8};
-  int rc = DR_OK;
+  int rc = DR_OK, timed = 0;
+  std::string last_msg;
   for (const auto& sh : shapes) {
     for (int k : ctas) {
       if (k > sh[3]) continue;
       dr_tune t{sh[1], sh[2], k, sh[0]};
-      if ((rc = dr_batch_set_tune(b, &t))) break;
-      for (int w = 0; w < 2; ++w) dr_batch_run(b, (dr_stream_t)s);
+      if ((rc = dr_batch_set_tune(b, &t))) break;  // host-side failure (tables, memory): give up
+      // a shape whose launch fails is skipped (timing an empty interval would make it "fastest")
+      bool ok = true;
+      for (int w = 0; w < 2 && ok; ++w) ok = dr_batch_run(b, (dr_stream_t)s) == DR_OK;
       std::vector<float> ms;
-      for (int it = 0; it < 5; ++it) {
+      for (int it = 0; it < 5 && ok; ++it) {
         cudaEventRecord(e0, s);
-        dr_batch_run(b, (dr_stream_t)s);
+        ok = dr_batch_run(b, (dr_stream_t)s) == DR_OK;
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float m = 0.f;
         cudaEventElapsedTime(&m, e0, e1);
         ms.push_back(m);
       }
+      if (!ok) {
+        last_msg = dr_last_error();
+        continue;
+      }
+      ++timed;
       std::sort(ms.begin(), ms.end());
       const double us = ms[ms.size() / 2] * 1e3;
       if (us < best_us) {
@@ -404,6 +412,8 @@ extern "C" int dr_batch_autotune(dr_batch* b, int mode, const char* cache_path, 
   cudaStreamDestroy(s);
   if (rc) return rc;
   if (int r = dr_sync_status(nullptr)) return r;
+  if (timed == 0)
+    return fail(DR_E_CUDA, "dr_batch_autotune: no launch shape ran (last error: %s)", last_msg.c_str());
   if (int r = dr_batch_set_tune(b, &best)) return r;
   if (cache_path && *cache_path) cache_store(cache_path, key, best, best_us);
   if (chosen) *chosen = best;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "dr_kernels.h"
@@ -460,6 +461,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
+// Polls of a wait for a bulk copy's completion.  A copy of a few tens of KB
+// lands within microseconds; this bound (each try_wait may suspend for a
+// hardware time slice) only ends a wait for a copy that never completes.  It
+// is separate from the lookback poll limit (dr_set_spin_limit), which tests
+// shorten on purpose: a CTA whose copy wait expired must neither read nor
+// re-arm that stage, and must not exit while the copy may still be writing.
+constexpr int64_t kCopyWaitPolls = int64_t(1) << 22;
+
 // --------------------------------------------------------------------------
 // warp building blocks
 // --------------------------------------------------------------------------
@@ -541,6 +550,41 @@ __device__ __forceinline__ T lookback(const S& slots, int64_t pred, int64_t lo, 
     pred -= 32 * G;
   }
   return run;
+}
+
+// ---------------------------------------------------------------------------
+// Host: resident CTAs per SM of a kernel on the current device.  Launch
+// attributes (the dynamic shared-memory opt-in) are per device, so they are set
+// once per device, with the result cached per device, under a lock.
+// ---------------------------------------------------------------------------
+struct OccCache {
+  std::mutex mu;
+  int per_sm[64] = {};
+};
+
+// Returns the resident CTAs per SM (>= 1), or 0 if the device index is out of
+// range or the attribute could not be set (the caller reports a launch error).
+template <typename K>
+int resident_ctas(OccCache& c, K* kernel, int threads, int dyn_smem) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> g(c.mu);
+  if (!c.per_sm[dev]) {
+    if (dyn_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem) != cudaSuccess)
+      return 0;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, dyn_smem) != cudaSuccess) return 0;
+    c.per_sm[dev] = per > 0 ? per : 1;
+  }
+  return c.per_sm[dev];
+}
+
+inline int current_sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
 }
 
 }  // namespace dr

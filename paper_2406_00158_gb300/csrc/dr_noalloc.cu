@@ -38,6 +38,7 @@ extern "C" int dr_dot_f32_noalloc(int nseg, const int64_t* lens, const float* co
                                   const float* const* y_segs, float init, float* dev_result,
                                   dr_stream_t stream) {
   using namespace dr;
+  clear_error();
   const char* who = "dr_dot_f32_noalloc";
   if (nseg < 1 || !lens || !x_segs || !y_segs || !dev_result)
     return fail(DR_E_INVAL, "%s: need nseg >= 1, lens, x_segs, y_segs, dev_result", who);

@@ -347,6 +347,7 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
     int vec = 0, vtiles = 0;
 
     // ---- R phase: dot partial and scan aggregate of tile t
+    bool copy_lost = false;  // this thread's wait for the stage's bulk copies expired
     if (haveR) {
       const BTile bt = P.tiles[t];
       const BPiece pc = P.pieces[bt.piece];
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
       cur = LaTile{pc.x, pc.y, bt.off, pc.len, bv.first_tile, pc.vec_ok != 0 && pc.len - bt.off >= G::TILE};
       float x[CH][4], pr[CH][4];
       if (cur.full) {
-        mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, P.spin_limit, P.status);
+        copy_lost = !mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, kCopyWaitPolls, P.status);
         const char* st = s_stage + sidx * G::STAGE;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
@@ -394,7 +395,15 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
     }
     long long tnew = P.ntiles;
     if (tid == 0 && tk1 < P.ntiles) tnew = (long long)atomicAdd(&hdr->ticket, 1ull);
-    __syncthreads();
+    if (__syncthreads_or(copy_lost)) {
+      // A bulk copy did not complete within its bound (DR_E_TIMEOUT is recorded):
+      // no stage is read or re-armed any more; wait, again bounded, for copies
+      // that may still be in flight into either stage, then leave.
+      if (tid == 0)
+        for (int d = 0; d < 2; ++d) mbar_wait(&s_bar[d], (parity >> d) & 1u, kCopyWaitPolls, P.status);
+      __syncthreads();
+      break;
+    }
 
     float prefix = 0.f;
     if (warp == 0) {
@@ -511,12 +520,9 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
 template <int CH, int MINB>
 cudaError_t go_la(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s) {
   using G = LaGeom<CH>;
-  static int per = 0;
-  if (!per) {
-    cudaFuncSetAttribute(k_batch_la<CH, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_la<CH, MINB>, LT, G::SMEM);
-    if (per < 1) per = 1;
-  }
+  static OccCache occ;
+  const int per = resident_ctas(occ, k_batch_la<CH, MINB>, LT, G::SMEM);
+  if (per <= 0) return cudaErrorInvalidConfiguration;
   const int k = ctas_per_sm < per ? ctas_per_sm : per;
   int64_t grid = (int64_t)sms * (k > 0 ? k : 1);
   if (grid > p.ntiles) grid = p.ntiles > 0 ? p.ntiles : 1;
@@ -526,11 +532,9 @@ cudaError_t go_la(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s
 
 template <int THREADS, int CH>
 cudaError_t go(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s) {
-  static int per = 0;
-  if (!per) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<THREADS, CH>, THREADS, 0);
-    if (per < 1) per = 1;
-  }
+  static OccCache occ;
+  const int per = resident_ctas(occ, k_batch<THREADS, CH>, THREADS, 0);
+  if (per <= 0) return cudaErrorInvalidConfiguration;
   const int k = ctas_per_sm < per ? ctas_per_sm : per;
   int64_t grid = (int64_t)sms * (k > 0 ? k : 1);
   if (grid > p.ntiles) grid = p.ntiles > 0 ? p.ntiles : 1;

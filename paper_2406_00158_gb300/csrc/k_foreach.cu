@@ -315,25 +315,19 @@ __global__ void __launch_bounds__(FT) k_transform(const __grid_constant__ Transf
   }
 }
 
-// Resident-CTA grid of a kernel (queried once per kernel instance and device).
+// Resident-CTA grid of a kernel (occupancy queried once per kernel instance and
+// device), capped by the tile count.
 template <typename K>
-int resident_grid(K kernel, int64_t ntiles) {
-  static int cached[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int& g = cached[dev & 63];
-  if (g == 0) {
-    int sms = 0, per = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, FT, 0);
-    g = sms * (per > 0 ? per : 1);
-  }
+int resident_grid(OccCache& occ, K* kernel, int64_t ntiles) {
+  const int per = resident_ctas(occ, kernel, FT, 0);
+  const int64_t g = (int64_t)current_sm_count() * (per > 0 ? per : 1);
   return (int)(ntiles < g ? ntiles : g);
 }
 
 template <typename T, int FN>
 cudaError_t run_fe(const ForEachParams& p, cudaStream_t s) {
-  const int grid = resident_grid(k_for_each<T, FN>, p.ntiles);
+  static OccCache occ;
+  const int grid = resident_grid(occ, k_for_each<T, FN>, p.ntiles);
   k_for_each<T, FN><<<grid, FT, 0, s>>>(p);
   return cudaGetLastError();
 }
@@ -352,7 +346,8 @@ cudaError_t run_fe_t(const ForEachParams& p, cudaStream_t s) {
 
 template <typename T, int KIND>
 cudaError_t run_tr(const TransformParams& p, cudaStream_t s) {
-  const int grid = resident_grid(k_transform<T, KIND>, p.ntiles);
+  static OccCache occ;
+  const int grid = resident_grid(occ, k_transform<T, KIND>, p.ntiles);
   k_transform<T, KIND><<<grid, FT, 0, s>>>(p);
   return cudaGetLastError();
 }

@@ -280,11 +280,12 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     const bool haveR = t < P.ntiles, haveS = tprev >= 0;
 
     // ---- R phase: aggregate of tile t (from its stage; ragged tiles load directly)
+    bool copy_lost = false;  // this thread's wait for the stage's bulk copy expired
     if (haveR) {
       const TileRef rr = tile_ref<T, REV>(P, t);
       T x[SCH][V], wx[SCH];
       if (rr.full) {
-        mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, P.spin_limit, P.status);
+        copy_lost = !mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, kCopyWaitPolls, P.status);
         const char* st = s_stage + sidx * kTileBytes;
 #pragma unroll
         for (int c = 0; c < SCH; ++c) {
@@ -312,7 +313,15 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     const long long tlast = tk[kStages - 1];
     long long tnew = P.ntiles;
     if (tid == 0 && tlast < P.ntiles) tnew = (long long)atomicAdd(&hdr->ticket, 1ull);
-    __syncthreads();
+    if (__syncthreads_or(copy_lost)) {
+      // A bulk copy did not complete within its bound (DR_E_TIMEOUT is recorded):
+      // no stage is read or re-armed any more; wait, again bounded, for the
+      // copies that may still be in flight into either stage, then leave.
+      if (tid == 0)
+        for (int d = 0; d < kStages; ++d) mbar_wait(&s_bar[d], (parity >> d) & 1u, kCopyWaitPolls, P.status);
+      __syncthreads();
+      break;
+    }
 
     T prefix = ident;
     if (warp == 0) {
@@ -399,7 +408,9 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     __syncthreads();
   }
 
-  // ---- exit (no copy is in flight: every staged ticket left is past the end): the last CTA restores the header for the next launch
+  // ---- exit (no copy is in flight: every staged ticket left is past the end, or
+  // the abort path above drained both stages): the last CTA restores the header
+  // for the next launch
   if (tid == 0) {
     __threadfence();
     if (atomicAdd(&hdr->done, 1u) == gridDim.x - 1) {
@@ -413,19 +424,10 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
 
 template <typename T, int OP, int KIND, bool REV, bool EXCL>
 cudaError_t go(const ScanParams& p, int grid, cudaStream_t s) {
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaFuncSetAttribute(k_scan<T, OP, KIND, REV, EXCL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem_bytes());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan<T, OP, KIND, REV, EXCL>, ST, smem_bytes());
-    if (per_sm <= 0) per_sm = 1;
-  }
-  if (grid <= 0) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    grid = sms * per_sm;
-  }
+  static OccCache occ;
+  const int per_sm = resident_ctas(occ, k_scan<T, OP, KIND, REV, EXCL>, ST, smem_bytes());
+  if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+  if (grid <= 0) grid = current_sm_count() * per_sm;
   if (p.ntiles < grid) grid = (int)(p.ntiles > 0 ? p.ntiles : 1);
   k_scan<T, OP, KIND, REV, EXCL><<<grid, ST, smem_bytes(), s>>>(p);
   return cudaGetLastError();
