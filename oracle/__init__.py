@@ -15,6 +15,7 @@ import ctypes
 import os
 import subprocess
 import threading
+from fractions import Fraction
 
 import numpy as np
 
@@ -62,6 +63,13 @@ _SIGS = {
     "oracle_sort_i32": (None, [_P, _I64]),
     "oracle_sort_i64": (None, [_P, _I64]),
     "oracle_partition_sort_i64": (None, [ctypes.c_int, _P, _P, _P]),
+    "oracle_scan_i64": (None, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P]),
+    "oracle_scan_i32": (None, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_int32, _P]),
+    "oracle_scan_f64": (None, [_P, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P]),
+    "oracle_reduce_i64": (ctypes.c_int64, [_P, _I64, ctypes.c_int, ctypes.c_int64]),
+    "oracle_reduce_i32": (ctypes.c_int32, [_P, _I64, ctypes.c_int, ctypes.c_int32]),
+    "oracle_reduce_f64": (ctypes.c_double, [_P, _I64, ctypes.c_int, ctypes.c_double]),
+    "oracle_sum_expansion_f64": (_I64, [_P, _I64, _P, _I64]),
 }
 
 
@@ -344,3 +352,121 @@ def partition_sort_i64(lens, x) -> np.ndarray:
     out = np.empty_like(x)
     lib().oracle_partition_sort_i64(int(lens.size), _p(lens), _p(x), _p(out))
     return out
+
+
+# ---------------------------------------------------------------------------
+# the other associative operators (Sec. 4.3: the footnote to "reduce"; the last
+# paragraph of "inclusive_scan" for exclusive_scan)
+# ---------------------------------------------------------------------------
+
+OPS = {"plus": 0, "mul": 1, "min": 2, "max": 3}
+
+
+def identity(op: str, dtype):
+    """The identity element of op for an element type (min / max: the type's
+    largest / lowest value, infinities for floats)."""
+    dt = np.dtype(dtype)
+    if op == "plus":
+        return dt.type(0)
+    if op == "mul":
+        return dt.type(1)
+    if np.issubdtype(dt, np.floating):
+        return dt.type(np.inf if op == "min" else -np.inf)
+    info = np.iinfo(dt)
+    return dt.type(info.max if op == "min" else info.min)
+
+
+def scan(x, op: str = "plus", exclusive: bool = False, init=None):
+    """Sequential scan of the concatenation with op in {plus, min, max}:
+    inclusive y_i = init op x_0 op ... op x_i (init defaults to the identity),
+    exclusive y_0 = init, y_i = init op x_0 op ... op x_{i-1}.  int64 / int32
+    wrap for plus; fp32 / fp64 run in FP64 (plus rounds in FP64 at every step,
+    min / max select exactly) and return FP64."""
+    x = np.asarray(x)
+    if init is None:
+        init = identity(op, x.dtype)
+    mode = 1 if exclusive else 0
+    if x.dtype == np.int64:
+        xc = _c(x, np.int64)
+        y = np.empty_like(xc)
+        lib().oracle_scan_i64(_p(xc), xc.size, OPS[op], mode, int(init), _p(y))
+    elif x.dtype == np.int32:
+        xc = _c(x, np.int32)
+        y = np.empty_like(xc)
+        lib().oracle_scan_i32(_p(xc), xc.size, OPS[op], mode, int(init), _p(y))
+    else:
+        xc = _c(x, np.float64)
+        y = np.empty_like(xc)
+        lib().oracle_scan_f64(_p(xc), xc.size, OPS[op], mode, float(init), _p(y))
+    return y
+
+
+def reduce(x, op: str = "plus", init=None):
+    """init op x_0 op ... op x_{n-1} over the concatenation (Algorithm 3's
+    result).  Integers: exact (wrapping plus / multiply).  Floats: min / max
+    exact; plus returns the EXACT sum as a Fraction (see sum_exact)."""
+    x = np.asarray(x)
+    if init is None:
+        init = identity(op, x.dtype)
+    if x.dtype == np.int64:
+        xc = _c(x, np.int64)
+        return int(lib().oracle_reduce_i64(_p(xc), xc.size, OPS[op], int(init)))
+    if x.dtype == np.int32:
+        xc = _c(x, np.int32)
+        return int(lib().oracle_reduce_i32(_p(xc), xc.size, OPS[op], int(init)))
+    if op == "plus":
+        return sum_exact(np.concatenate([[float(init)], np.asarray(x, np.float64)]))
+    xc = _c(x, np.float64)
+    return float(lib().oracle_reduce_f64(_p(xc), xc.size, OPS[op], float(init)))
+
+
+def sum_exact(x) -> Fraction:
+    """The exact sum of the doubles x (a rational): the oracle builds a
+    non-overlapping expansion with error-free two-sums (Shewchuk's
+    Grow-Expansion) and the expansion's terms are added as Fractions."""
+    xc = _c(x, np.float64)
+    cap = 2100  # a double expansion has at most ~2098 non-overlapping terms
+    parts = np.empty(cap, np.float64)
+    k = lib().oracle_sum_expansion_f64(_p(xc), xc.size, _p(parts), cap)
+    assert k >= 0
+    return sum((Fraction(float(v)) for v in parts[:k]), Fraction(0))
+
+
+# ---------------------------------------------------------------------------
+# take / drop (Sec. 4.4 "Take and Drop": both trim the segment list)
+# ---------------------------------------------------------------------------
+
+def trim_segments(lens, f: int, l: int):
+    """The segments of a range restricted to its elements [f, l): for every
+    segment k covering global indices [s_k, s_k + len_k), the part inside
+    [f, l) as (k, offset in segment k, length); segments left empty are
+    dropped.  Bounds are clamped to [0, n]."""
+    n = int(sum(int(v) for v in lens))
+    f = max(0, min(int(f), n))
+    l = max(f, min(int(l), n))
+    out, s = [], 0
+    for k, L in enumerate(lens):
+        L = int(L)
+        a, b = max(f, s), min(l, s + L)
+        if b > a:
+            out.append((k, a - s, b - a))
+        s += L
+    return out
+
+
+def take_segments(lens, l: int):
+    """take(l): the first l elements (trim to [0, l))."""
+    return trim_segments(lens, 0, l)
+
+
+def drop_segments(lens, f: int):
+    """drop(f): all but the first f elements (trim to [f, n))."""
+    return trim_segments(lens, f, sum(int(v) for v in lens))
+
+
+def gather_segments(x, lens, pieces):
+    """The elements of the concatenation x (segment sizes lens) that the pieces
+    (segment, offset, length) name, in order."""
+    starts = np.concatenate([[0], np.cumsum(np.asarray(lens, np.int64))])
+    parts = [np.asarray(x)[starts[k] + o: starts[k] + o + L] for k, o, L in pieces]
+    return np.concatenate(parts) if parts else np.asarray(x)[:0]

@@ -99,6 +99,113 @@ void oracle_segmented_scan_alg4_i64(int nseg, const int64_t* lens, const int64_t
 }
 
 // --------------------------------------------------------------------------
+// Scans and reduces with the other associative operators of Sec. 4.3 (the
+// footnote to "reduce": any such operator; the last paragraph of
+// "inclusive_scan": exclusive_scan is the same algorithm shifted by one, with
+// an initial value).  op: 0 = plus, 2 = min, 3 = max (1 = multiply, reduce
+// only).  min(a, b) selects b only when b < a, max(a, b) selects b only when
+// a < b.  Integer plus and multiply wrap in the unsigned type of the same
+// width.  mode 0: inclusive, y_i = init op x_0 op ... op x_i (the identity as
+// init gives the plain inclusive scan); mode 1: exclusive, y_0 = init,
+// y_i = init op x_0 op ... op x_{i-1}.
+// --------------------------------------------------------------------------
+}  // extern "C"
+
+template <typename T, typename U>
+static T op_apply(int op, T a, T b) {
+  switch (op) {
+    case 0: return (T)(U)((U)a + (U)b);
+    case 1: return (T)(U)((U)a * (U)b);
+    case 2: return b < a ? b : a;
+    default: return a < b ? b : a;
+  }
+}
+
+template <typename T, typename U>
+static void scan_op(const T* x, int64_t n, int op, int mode, T init, T* y) {
+  T acc = init;
+  for (int64_t i = 0; i < n; ++i) {
+    if (mode == 1) {
+      y[i] = acc;
+      acc = op_apply<T, U>(op, acc, x[i]);
+    } else {
+      acc = op_apply<T, U>(op, acc, x[i]);
+      y[i] = acc;
+    }
+  }
+}
+
+template <typename T, typename U>
+static T reduce_op(const T* x, int64_t n, int op, T init) {
+  T acc = init;
+  for (int64_t i = 0; i < n; ++i) acc = op_apply<T, U>(op, acc, x[i]);
+  return acc;
+}
+
+// Floating-point operators in FP64 (plus rounds at every step; min / max select).
+struct F64U {};
+template <>
+double op_apply<double, F64U>(int op, double a, double b) {
+  switch (op) {
+    case 0: return a + b;
+    case 1: return a * b;
+    case 2: return b < a ? b : a;
+    default: return a < b ? b : a;
+  }
+}
+
+extern "C" {
+
+void oracle_scan_i64(const int64_t* x, int64_t n, int op, int mode, int64_t init, int64_t* y) {
+  scan_op<int64_t, uint64_t>(x, n, op, mode, init, y);
+}
+void oracle_scan_i32(const int32_t* x, int64_t n, int op, int mode, int32_t init, int32_t* y) {
+  scan_op<int32_t, uint32_t>(x, n, op, mode, init, y);
+}
+void oracle_scan_f64(const double* x, int64_t n, int op, int mode, double init, double* y) {
+  scan_op<double, F64U>(x, n, op, mode, init, y);
+}
+int64_t oracle_reduce_i64(const int64_t* x, int64_t n, int op, int64_t init) {
+  return reduce_op<int64_t, uint64_t>(x, n, op, init);
+}
+int32_t oracle_reduce_i32(const int32_t* x, int64_t n, int op, int32_t init) {
+  return reduce_op<int32_t, uint32_t>(x, n, op, init);
+}
+double oracle_reduce_f64(const double* x, int64_t n, int op, double init) {
+  return reduce_op<double, F64U>(x, n, op, init);
+}
+
+// The exact sum of n doubles as a non-overlapping expansion (J. R. Shewchuk,
+// "Adaptive precision floating-point arithmetic and fast robust geometric
+// predicates", Discrete Comput. Geom. 18, 1997: Grow-Expansion with zero
+// elimination).  Each new term is added into the list of partials by
+// error-free two-sums (hi = a + b rounded; lo = the exact rounding error,
+// recovered with the magnitude-ordered Fast-Two-Sum); nonzero errors stay in
+// the list, so sum(partials) equals sum(x) exactly, barring overflow.  Writes
+// at most `cap` partials (smallest first) and returns their count, or -1 if
+// more would be needed.
+int64_t oracle_sum_expansion_f64(const double* x, int64_t n, double* partials, int64_t cap) {
+  std::vector<double> p;
+  for (int64_t i = 0; i < n; ++i) {
+    double v = x[i];
+    size_t k = 0;
+    for (size_t j = 0; j < p.size(); ++j) {
+      double a = v, b = p[j];
+      if (std::fabs(a) < std::fabs(b)) std::swap(a, b);
+      const double hi = a + b;
+      const double lo = b - (hi - a);
+      if (lo != 0.0) p[k++] = lo;
+      v = hi;
+    }
+    p.resize(k);
+    p.push_back(v);
+  }
+  if ((int64_t)p.size() > cap) return -1;
+  for (size_t j = 0; j < p.size(); ++j) partials[j] = p[j];
+  return (int64_t)p.size();
+}
+
+// --------------------------------------------------------------------------
 // Reverse inclusive scan (adjoint of inclusive_scan):
 //   g_x[j] = sum_{i >= j} g_y[i]
 // --------------------------------------------------------------------------

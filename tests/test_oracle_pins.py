@@ -584,3 +584,151 @@ def test_black_scholes_fp32_bound_holds_for_a_plain_fp32_evaluation():
     bound = T.black_scholes_bound(S, X, Tm, r, sig, aux)
     assert np.all(np.abs(call - ec) <= bound) and np.all(np.abs(put - ep) <= bound)
     assert np.median(bound / (S + aux[:, 3])) < 2e-5
+
+
+# ----------------------------------------------------------------------------------
+# the other associative operators: exclusive scans with init, MIN / MAX scans,
+# reduce over every operator and element type (Sec. 4.3)
+# ----------------------------------------------------------------------------------
+
+def _wrap(v, bits):
+    v %= 2 ** bits
+    return v - 2 ** bits if v >= 2 ** (bits - 1) else v
+
+
+@pytest.mark.parametrize("n,init", [(0, 7), (1, 7), (4097, -3), (10_000, 0)])
+def test_exclusive_scan_of_ones_is_init_plus_iota(n, init):
+    y = oracle.scan(np.ones(n, np.int64), "plus", exclusive=True, init=init)
+    assert np.array_equal(y, init + np.arange(n, dtype=np.int64))
+    y32 = oracle.scan(np.ones(n, np.int32), "plus", exclusive=True, init=init)
+    assert y32.dtype == np.int32 and np.array_equal(y32, init + np.arange(n, dtype=np.int32))
+
+
+@pytest.mark.parametrize("dt,bits", [(np.int64, 64), (np.int32, 32)])
+def test_scan_plus_bruteforce_wraps(dt, bits):
+    lo, hi = (-2 ** 62, 2 ** 62) if bits == 64 else (-2 ** 30, 2 ** 30)
+    x = inputs.uniform_int64(RNG_KEY + 1, 12, lo, hi).astype(dt)
+    init = int(x[0]) // 3
+    yi = oracle.scan(x, "plus", exclusive=False, init=init)
+    ye = oracle.scan(x, "plus", exclusive=True, init=init)
+    for i in range(x.size):
+        assert int(yi[i]) == _wrap(init + sum(int(v) for v in x[:i + 1]), bits)
+        assert int(ye[i]) == _wrap(init + sum(int(v) for v in x[:i]), bits)
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_minmax_scan_of_a_permutation_bruteforce(op):
+    n = 300
+    r = inputs.raw_u64(RNG_KEY + 2, n)
+    perm = np.argsort(r, kind="stable").astype(np.int64)   # a permutation of 0..n-1
+    f = max if op == "max" else min
+    for excl in (False, True):
+        for init in (None, 150):
+            y = oracle.scan(perm, op, exclusive=excl, init=init)
+            start = (-(2 ** 63) if op == "max" else 2 ** 63 - 1) if init is None else init
+            for i in range(n):
+                pre = [int(v) for v in perm[:i + (0 if excl else 1)]]
+                assert int(y[i]) == f([start] + pre)
+    if op == "max":   # a permutation's running max reaches n-1 exactly where n-1 sits
+        y = oracle.scan(perm, "max")
+        k = int(np.argmax(perm))
+        assert int(y[k]) == n - 1 and (k == 0 or int(y[k - 1]) < n - 1)
+
+
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_minmax_scan_floats_bruteforce(op):
+    x = inputs.uniform_pm1_f32(RNG_KEY + 3, 200).astype(np.float64)
+    f = max if op == "max" else min
+    y = oracle.scan(x, op)
+    ye = oracle.scan(x, op, exclusive=True, init=0.25)
+    for i in range(x.size):
+        assert y[i] == f(float(v) for v in x[:i + 1])
+        assert ye[i] == f([0.25] + [float(v) for v in x[:i]])
+    assert oracle.scan(x[:0], op).size == 0
+    assert oracle.scan(x[:1], op, exclusive=True)[0] == (-np.inf if op == "max" else np.inf)
+
+
+def test_scan_plus_f64_small_integers_exact():
+    x = inputs.uniform_int64(RNG_KEY + 4, 5000, -100, 100)
+    y = oracle.scan(x.astype(np.float64), "plus", exclusive=True, init=2.0)
+    assert np.array_equal(y, 2.0 + np.concatenate([[0], np.cumsum(x)[:-1]]).astype(np.float64))
+
+
+@pytest.mark.parametrize("dt,bits", [(np.int64, 64), (np.int32, 32)])
+def test_reduce_integers_bruteforce(dt, bits):
+    lo, hi = (-2 ** 62, 2 ** 62) if bits == 64 else (-2 ** 30, 2 ** 30)
+    x = inputs.uniform_int64(RNG_KEY + 5, 64, lo, hi).astype(dt)
+    xs = [int(v) for v in x]
+    assert oracle.reduce(x, "plus", init=5) == _wrap(5 + sum(xs), bits)
+    assert oracle.reduce(x, "max", init=-7) == max([-7] + xs)
+    assert oracle.reduce(x, "min", init=7) == min([7] + xs)
+    assert oracle.reduce(x, "max") == max(xs) and oracle.reduce(x, "min") == min(xs)
+    small = inputs.uniform_int64(RNG_KEY + 6, 20, -3, 4).astype(dt)
+    assert oracle.reduce(small, "mul", init=1) == _wrap(math.prod(int(v) for v in small), bits)
+    n = 70_001
+    assert oracle.reduce(np.arange(n, dtype=dt), "plus") == _wrap(n * (n - 1) // 2, bits)
+
+
+def test_reduce_float_minmax_and_empty():
+    x = inputs.uniform_pm1_f32(RNG_KEY + 7, 1000)
+    assert oracle.reduce(x, "max") == max(float(v) for v in x)
+    assert oracle.reduce(x, "min", init=-2.0) == -2.0
+    assert oracle.reduce(x[:0], "max", init=3.5) == 3.5
+    assert oracle.reduce(x[:0], "plus", init=1.25) == Fraction(5, 4)
+
+
+def test_sum_exact_against_rationals_and_fsum():
+    # huge cancellation: every naive order loses the small terms
+    x = np.array([1e16, 1.0, -1e16, 3.0, 2.0 ** -60, -3.0], np.float64)
+    assert oracle.sum_exact(x) == Fraction(1) + Fraction(2) ** -60
+    for key in range(5):
+        r = inputs.uniform01_f64(RNG_KEY + 10 + key, 400)
+        e = inputs.uniform_int64(RNG_KEY + 20 + key, 400, -60, 60)
+        v = (2 * r - 1) * np.exp2(e.astype(np.float64))    # magnitudes over 120 binades
+        exact = sum((Fraction(float(t)) for t in v), Fraction(0))
+        got = oracle.sum_exact(v)
+        assert got == exact
+        assert float(got) == math.fsum(v)   # both correctly rounded
+    # reduce(plus) of floats = init plus the exact sum
+    v = inputs.uniform_pm1_f32(RNG_KEY + 30, 3000)
+    assert oracle.reduce(v, "plus", init=0.5) == Fraction(1, 2) + sum((Fraction(float(t)) for t in v), Fraction(0))
+
+
+# ----------------------------------------------------------------------------------
+# take / drop via trimmed segments (Sec. 4.4 "Take and Drop")
+# ----------------------------------------------------------------------------------
+
+def _owner_runs(lens, f, l):
+    """Brute force: the owner (segment, offset) of every global index in [f, l),
+    merged into maximal runs of one segment."""
+    owners = []
+    for k, L in enumerate(lens):
+        owners.extend((k, j) for j in range(L))
+    runs = []
+    for i in range(max(0, f), min(l, len(owners))):
+        k, j = owners[i]
+        if runs and runs[-1][0] == k:
+            runs[-1] = (k, runs[-1][1], runs[-1][2] + 1)
+        else:
+            runs.append((k, j, 1))
+    return runs
+
+
+@pytest.mark.parametrize("lens", [[3, 0, 4, 1, 0], [5], [0, 0, 2], [1, 1, 1, 1]])
+def test_trim_segments_bruteforce_every_window(lens):
+    n = sum(lens)
+    for f in range(-1, n + 2):
+        for l in range(-1, n + 3):
+            assert oracle.trim_segments(lens, f, l) == _owner_runs(lens, f, l), (f, l)
+    for l in range(n + 3):
+        assert oracle.take_segments(lens, l) == _owner_runs(lens, 0, l)
+    for f in range(n + 3):
+        assert oracle.drop_segments(lens, f) == _owner_runs(lens, f, n)
+
+
+def test_trim_gathers_the_slice():
+    lens = [10, 0, 25, 7, 0, 13]
+    x = np.arange(55, dtype=np.int64) * 3 + 1
+    for f, l in [(0, 55), (9, 11), (10, 35), (34, 36), (50, 80), (20, 20)]:
+        got = oracle.gather_segments(x, lens, oracle.trim_segments(lens, f, l))
+        assert np.array_equal(got, x[max(0, f):min(l, 55)])
