@@ -117,6 +117,17 @@ int dr_version(void);
  * launched earlier on this device; its results are invalid) or DR_E_CUDA. */
 int dr_sync_status(dr_stream_t stream);
 
+/* Tile geometry of a kernel family (host only; no device needed):
+ *   *tile_elems = the elements of `dtype` one tile covers -- the unit of the
+ *     scan's carry chain (one lookback hop per tile), of the reduce's
+ *     per-thread accumulation, of for_each / transform and of a sort pass;
+ *   *ctas_per_sm = the CTAs per SM of the kernel's grid when it is fixed by
+ *     design (the reduce: its grid fixes the summation tree), else 0 (a
+ *     persistent grid sized by occupancy).
+ * Either output may be NULL.  Rounding-error bounds are derived from these. */
+enum dr_kernel_family { DR_K_SCAN = 0, DR_K_REDUCE = 1, DR_K_FOREACH = 2, DR_K_SORT = 3 };
+int dr_kernel_geometry(int kernel, int dtype, int64_t* tile_elems, int* ctas_per_sm);
+
 /* Upper bound on the polls of every device-side wait (scan lookback, batched
  * carry); each poll sleeps at most ~1 us.  Default 1<<21 (~1-2 s).  polls>=1. */
 int dr_set_spin_limit(int64_t polls);
@@ -194,6 +205,17 @@ int dr_view_transform(const dr_view* base, int op, double arg, dr_view** out);
  * operands' boundaries (Sec. 4.4 "Zip").  A zip is not single-valued until a
  * binary function is applied with dr_view_zip_transform. */
 int dr_view_zip(const dr_view* a, const dr_view* b, dr_view** out);
+
+/* zip with flags.  DR_ZIP_STRICT_ALIGN refuses operands that are not aligned
+ * with DR_E_ALIGN instead of re-cutting them: the distributed-memory runtime of
+ * Sec. 4.3 ("inclusive_scan") and Sec. 4.4 ("Zip") prohibits zips of
+ * non-aligned ranges, where aligned means the same number of segments with
+ * corresponding segments of the same size (and memory locale; here every
+ * segment is in one GPU's memory).  The segments compared are those the views
+ * cover (after take / drop), empty segments not counted.  flags 0 is
+ * dr_view_zip. */
+#define DR_ZIP_STRICT_ALIGN 1
+int dr_view_zip_ex(const dr_view* a, const dr_view* b, int flags, dr_view** out);
 
 /* transform of a zip with a binary function: element i = op(a_i, b_i), e.g.
  * DR_MUL for the dot product of Algorithm 1. */

@@ -24,6 +24,9 @@ DR_F32, DR_F64, DR_I64, DR_I32 = range(4)
 DR_PLUS, DR_MUL, DR_MIN, DR_MAX = range(4)
 # enum dr_unop
 DR_U_SCALE, DR_U_ADD, DR_U_NEG, DR_U_ABS, DR_U_SQUARE = range(5)
+# enum dr_kernel_family
+DR_K_SCAN, DR_K_REDUCE, DR_K_FOREACH, DR_K_SORT = range(4)
+DR_ZIP_STRICT_ALIGN = 1
 
 
 class dr_piece(ctypes.Structure):
@@ -55,6 +58,7 @@ PROTOTYPES = {
     "dr_last_error": (ctypes.c_char_p, []),
     "dr_version": (_I, []),
     "dr_sync_status": (_I, [_P]),
+    "dr_kernel_geometry": (_I, [_I, _I, _PI64, _PI]),
     "dr_set_spin_limit": (_I, [_I64]),
     "dr_debug_skip_publish": (_I, [_I64]),
     "dr_block_lengths": (_I, [_I64, _I, _PI64]),
@@ -71,6 +75,7 @@ PROTOTYPES = {
     "dr_view_of": (_I, [_P, _PP]),
     "dr_view_transform": (_I, [_P, _I, _D, _PP]),
     "dr_view_zip": (_I, [_P, _P, _PP]),
+    "dr_view_zip_ex": (_I, [_P, _P, _I, _PP]),
     "dr_view_zip_transform": (_I, [_P, _I, _PP]),
     "dr_view_zipn": (_I, [_I, _PP, _PP]),
     "dr_view_take": (_I, [_P, _I64, _PP]),
@@ -124,6 +129,13 @@ def lib():
 
 def last_error() -> str:
     return (lib().dr_last_error() or b"").decode()
+
+
+def kernel_geometry(kernel: int, dtype: int) -> tuple[int, int]:
+    """(tile elements, fixed CTAs per SM or 0) of a kernel family for a dtype."""
+    t, c = ctypes.c_int64(), ctypes.c_int()
+    call("dr_kernel_geometry", int(kernel), int(dtype), ctypes.byref(t), ctypes.byref(c))
+    return t.value, c.value
 
 
 def call(name: str, *args) -> None:

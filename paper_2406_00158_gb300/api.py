@@ -185,9 +185,14 @@ class View:
              ctypes.byref(h))
         return View(h, [self])
 
-    def zip(self, other: "View") -> "View":
+    def zip(self, other: "View", strict_align: bool = False) -> "View":
+        """zip(self, other); with strict_align=True, operands that are not
+        aligned are refused (DR_E_ALIGN) instead of re-cut."""
         h = _handle_out()
-        call("dr_view_zip", self.handle, other.handle, ctypes.byref(h))
+        if strict_align:
+            call("dr_view_zip_ex", self.handle, other.handle, L.DR_ZIP_STRICT_ALIGN, ctypes.byref(h))
+        else:
+            call("dr_view_zip", self.handle, other.handle, ctypes.byref(h))
         return View(h, [self, other])
 
     @classmethod

@@ -279,6 +279,26 @@ extern "C" int dr_sync_status(dr_stream_t stream) {
   return DR_OK;
 }
 
+extern "C" int dr_kernel_geometry(int kernel, int dtype, int64_t* tile_elems, int* ctas_per_sm) {
+  clear_error();
+  if (!valid_dtype(dtype)) return fail(DR_E_DTYPE, "dr_kernel_geometry: unknown dtype %d", dtype);
+  int64_t t = 0;
+  int per = 0;
+  switch (kernel) {
+    case DR_K_SCAN: t = scan_tile_elems(dtype); break;
+    case DR_K_REDUCE:
+      t = reduce_tile_elems(dtype);
+      per = reduce_ctas_per_sm();
+      break;
+    case DR_K_FOREACH: t = foreach_tile_elems(dtype); break;
+    case DR_K_SORT: t = sort_tile_elems(dtype); break;
+    default: return fail(DR_E_INVAL, "dr_kernel_geometry: unknown kernel family %d", kernel);
+  }
+  if (tile_elems) *tile_elems = t;
+  if (ctas_per_sm) *ctas_per_sm = per;
+  return DR_OK;
+}
+
 extern "C" int dr_set_spin_limit(int64_t polls) {
   clear_error();
   if (polls < 1) return fail(DR_E_INVAL, "spin limit must be >= 1 (got %lld)", (long long)polls);
@@ -510,6 +530,29 @@ extern "C" int dr_view_transform(const dr_view* base, int op, double arg, dr_vie
   w->npost++;
   *out = w;
   return DR_OK;
+}
+
+// Aligned operands (Sec. 4.4 "Zip"): the same number of (non-empty) segments
+// over the views' windows, with corresponding segments of equal size.
+static bool aligned(const dr_view* a, const dr_view* b) {
+  const std::vector<Seg> sa = a->leaf[0].vec->window(a->leaf[0].lo, a->leaf[0].hi);
+  const std::vector<Seg> sb = b->leaf[0].vec->window(b->leaf[0].lo, b->leaf[0].hi);
+  if (sa.size() != sb.size()) return false;
+  for (size_t k = 0; k < sa.size(); ++k)
+    if (sa[k].len != sb[k].len) return false;
+  return true;
+}
+
+extern "C" int dr_view_zip_ex(const dr_view* a, const dr_view* b, int flags, dr_view** out) {
+  clear_error();
+  if (!a || !b || !out) return fail(DR_E_INVAL, "dr_view_zip_ex: NULL argument");
+  if (flags & ~DR_ZIP_STRICT_ALIGN) return fail(DR_E_INVAL, "dr_view_zip_ex: unknown flags 0x%x", flags);
+  if (a->arity != 1 || b->arity != 1 || a->nleaf != 1 || b->nleaf != 1)
+    return fail(DR_E_UNSUPPORTED, "dr_view_zip_ex: operands must be (transformed) views of one vector each");
+  if ((flags & DR_ZIP_STRICT_ALIGN) && !aligned(a, b))
+    return fail(DR_E_ALIGN, "dr_view_zip_ex: operands are not aligned (segment counts or sizes differ) and "
+                            "strict alignment was requested");
+  return dr_view_zip(a, b, out);
 }
 
 extern "C" int dr_view_zip(const dr_view* a, const dr_view* b, dr_view** out) {

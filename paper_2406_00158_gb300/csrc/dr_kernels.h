@@ -223,6 +223,7 @@ cudaError_t launch_sort(SortParams& p, const SortLaunch& L, cudaStream_t s);
 
 // Resident-CTA count helpers (host).
 int reduce_grid(int dtype);
+int reduce_ctas_per_sm();
 int scan_grid(int dtype, int64_t ntiles);
 
 }  // namespace dr

@@ -39,6 +39,8 @@ int reduce_tile_elems(int dtype) {
 
 size_t reduce_ws_bytes(int grid) { return sizeof(WsHeader) + (size_t)grid * 8; }
 
+int reduce_ctas_per_sm() { return kreduce::RCTAS; }
+
 // Fixed grid: RCTAS CTAs per SM of the current device.
 int reduce_grid(int) {
   int dev = 0, sms = 0;

@@ -25,3 +25,17 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _guard_bands(request):
+    """After every GPU test: the sentinel bands around the segments the test
+    helpers allocated must be intact (no kernel wrote past a segment)."""
+    yield
+    if "gpu" not in request.keywords:
+        return
+    gu = sys.modules.get("tests.gpu_util")
+    if gu is None:
+        return
+    bad = gu.check_guards()
+    assert not bad, "guard band overwritten: " + "; ".join(bad)

@@ -136,14 +136,8 @@ def test_take_drop_trim_segments(lib):
             lo = min(f, 14)
             hi = min(14, lo + l)
             assert size == hi - lo
-            # brute force: owners of [lo, hi) grouped by segment
-            owners = [(k, j) for k, L_ in enumerate(lens) for j in range(L_)][lo:hi]
-            exp = []
-            for k, j in owners:
-                if exp and exp[-1][0] == k:
-                    exp[-1][4] += 1
-                else:
-                    exp.append([k, j, -1, 0, 1])
+            # the oracle's trimmed segment list (take(l) after drop(f) = trim to [lo, hi))
+            exp = [[k, o, -1, 0, n] for k, o, n in oracle.trim_segments(lens, lo, hi)]
             assert [list(p) for p in got] == exp
             lib.dr_view_destroy(t)
             lib.dr_view_destroy(d)
@@ -424,3 +418,49 @@ def test_scale_by_partner_validation(lib):
     _, my = make_vec([129], ptrs=[1 << 47])
     _, mg = make_vec([129], ptrs=[1 << 40])
     assert F(mx, my, g, mg, None, None) == L.DR_E_UNSUPPORTED
+
+
+def test_kernel_geometry_host_only(lib):
+    """Tile sizes the error bounds are derived from: 32 KB scan tiles (8192 fp32,
+    4096 int64), 16 KB reduce tiles with a fixed 4 CTAs per SM."""
+    assert L.kernel_geometry(L.DR_K_SCAN, L.DR_F32) == (8192, 0)
+    assert L.kernel_geometry(L.DR_K_SCAN, L.DR_I64) == (4096, 0)
+    assert L.kernel_geometry(L.DR_K_SCAN, L.DR_I32) == (8192, 0)
+    assert L.kernel_geometry(L.DR_K_REDUCE, L.DR_F32) == (4096, 4)
+    assert L.kernel_geometry(L.DR_K_REDUCE, L.DR_F64) == (2048, 4)
+    t, _ = L.kernel_geometry(L.DR_K_FOREACH, L.DR_F64)
+    assert t > 0 and L.kernel_geometry(L.DR_K_SORT, L.DR_F32)[0] > 0
+    tt = ctypes.c_int64()
+    assert lib.dr_kernel_geometry(9, L.DR_F32, ctypes.byref(tt), None) == L.DR_E_INVAL
+    assert lib.dr_kernel_geometry(L.DR_K_SCAN, 7, ctypes.byref(tt), None) == L.DR_E_DTYPE
+    assert lib.dr_kernel_geometry(L.DR_K_SCAN, L.DR_F32, None, None) == L.DR_OK
+
+
+def test_strict_align_zip(lib):
+    """DR_ZIP_STRICT_ALIGN refuses non-aligned operands (Sec. 4.4 "Zip": the
+    distributed-memory runtime prohibits them) and accepts aligned ones;
+    without the flag the zip re-cuts them as usual."""
+    def zip_ex(la, lb, flags, take=None):
+        _, ha = make_vec(la)
+        _, hb = make_vec(lb, ptrs=fake_ptrs(lb, base=1 << 40))
+        va, vb = view_of(ha), view_of(hb)
+        if take is not None:
+            ta, tb = ctypes.c_void_p(), ctypes.c_void_p()
+            assert lib.dr_view_take(va, take, ctypes.byref(ta)) == 0
+            assert lib.dr_view_take(vb, take, ctypes.byref(tb)) == 0
+            va, vb = ta, tb
+        z = ctypes.c_void_p()
+        rc = lib.dr_view_zip_ex(va, vb, flags, ctypes.byref(z))
+        if rc == 0:
+            lib.dr_view_destroy(z)
+        return rc
+    S = L.DR_ZIP_STRICT_ALIGN
+    assert zip_ex([4, 4], [4, 4], S) == L.DR_OK
+    assert zip_ex([4, 0, 4], [4, 4], S) == L.DR_OK            # empty segments are not counted
+    assert zip_ex([4, 4], [3, 5], S) == L.DR_E_ALIGN
+    assert "not aligned" in L.last_error()
+    assert zip_ex([8], [4, 4], S) == L.DR_E_ALIGN
+    assert zip_ex([4, 4], [3, 5], 0) == L.DR_OK               # re-cut without the flag
+    assert zip_ex([4, 4], [4, 6], S, take=6) == L.DR_OK       # aligned over the taken windows
+    assert zip_ex([4, 4], [4, 6], S) == L.DR_E_ALIGN          # but not over the whole vectors
+    assert zip_ex([4, 4], [4, 4], 2) == L.DR_E_INVAL

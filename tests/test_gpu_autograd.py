@@ -60,13 +60,36 @@ def test_scan_grad_full_size_vs_fp64_adjoint(ag):
     g = torch.cat([s.grad for s in segs]).cpu().numpy()
     ref = oracle.reverse_inclusive_scan_f64(w.astype(np.float64))
     absref = oracle.reverse_inclusive_scan_f64(np.abs(w).astype(np.float64))
-    tiles = G.tile_index(lens, 8192)
+    tiles = G.tile_index(lens, G.scan_tile(torch.float32))
     err = np.abs(g.astype(np.float64) - ref)
     assert np.all(err <= T.scan_bound(absref, tiles.max() - tiles))
     # forward values too
     y = torch.cat([t.detach() for t in ys]).cpu().numpy()
     yref, s = oracle.inclusive_scan_f32_f64(x)
     assert np.all(np.abs(y - yref) <= T.scan_bound(s, tiles))
+
+
+def test_scan_grad_full_size_exact_integer_valued(ag):
+    """n = 2^26 in 8 segments with x and y_bar integer-valued in {-1, 0, 1}: every
+    partial sum either kernel forms is a range sum of a walk whose prefixes span
+    less than 2^24 (checked), so the forward values and the gradient are exact
+    and must equal the oracle bit for bit."""
+    n = 1 << 26
+    lens = inputs.block_segments(n, 8)
+    xi = inputs.uniform_int64(inputs.SEED_GRAD + 7, n, -1, 2)
+    wi = inputs.uniform_int64(inputs.SEED_GRAD + 8, n, -1, 2)
+    fwd = oracle.inclusive_scan_i64(xi)
+    bwd = oracle.reverse_inclusive_scan_f64(wi.astype(np.float64))
+    for walk in (fwd, oracle.inclusive_scan_i64(wi)):
+        assert max(int(walk.max()), 0) - min(int(walk.min()), 0) < (1 << 24)
+    segs = split(torch.from_numpy(xi.astype(np.float32)).cuda(), lens)
+    ys = ag.inclusive_scan(segs)
+    wt = torch.from_numpy(wi.astype(np.float32)).cuda()
+    torch.autograd.backward(list(ys), list(wt.split(lens)))
+    y = torch.cat([t.detach() for t in ys]).cpu().numpy()
+    g = torch.cat([s.grad for s in segs]).cpu().numpy()
+    assert np.array_equal(y, fwd.astype(np.float32))
+    assert np.array_equal(g, bwd.astype(np.float32))
 
 
 @pytest.mark.parametrize("n,lx,ly", [(300, [100, 200], [300]), (1 << 22, None, None)])

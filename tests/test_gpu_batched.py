@@ -73,7 +73,7 @@ def test_batch_small_vs_oracle_repeat_graph_per_range(api, tune):
     dots.fill_(float("nan"))
     b.run_per_range()
     api.sync_status()
-    check(x, p, shapes, ys, dots, tile=8192)
+    check(x, p, shapes, ys, dots, tile=G.scan_tile(torch.float32))
 
 
 def test_batch_non_aligned_partner(api):
@@ -94,6 +94,34 @@ def test_batch_full_config_4096_vectors(api):
     b.run_graph()
     api.sync_status()
     check(x, p, shapes, ys, dots, tile=b.tune[0] * b.tune[1])
+
+
+def test_batch_full_config_exact_integer_valued(api):
+    """The 4096-vector batch with x and p integer-valued in {-1, 0, 1}: a vector
+    has at most 10^6 elements, so every partial sum of its scan and of its dot is
+    an integer below 2^24 in magnitude and exact in fp32.  The one-launch run
+    (graph replay) and the per-range baseline must both equal the oracle bit for
+    bit: the int64 scan per vector and the FP64 (here exact) dot."""
+    shapes = inputs.batch_shapes(inputs.SEED_BATCH, 4096)
+    tot = sum(map(sum, shapes))
+    x = inputs.uniform_int64(inputs.SEED_BATCH_X + 50, tot, -1, 2).astype(np.float32)
+    p = inputs.uniform_int64(inputs.SEED_BATCH_P + 50, tot, -1, 2).astype(np.float32)
+    xs, ps, ys = api.packed_vectors(x, shapes), api.packed_vectors(p, shapes), api.packed_vectors(None, shapes)
+    dots = torch.full((len(shapes),), float("nan"), dtype=torch.float32, device="cuda")
+    b = api.Batch(xs, ps, ys, dots)
+    starts = np.concatenate([[0], np.cumsum([sum(sh) for sh in shapes])])
+    for run in (b.run_graph, b.run_per_range):
+        dots.fill_(float("nan"))
+        run()
+        api.sync_status()
+        dh = dots.cpu().numpy()
+        yall = torch.cat([torch.cat(v.segments) for v in ys]).cpu().numpy()
+        for v in range(len(shapes)):
+            lo, hi = starts[v], starts[v + 1]
+            xv = x[lo:hi].astype(np.int64)
+            yref = oracle.inclusive_scan_i64(xv)
+            assert np.array_equal(yall[lo:hi], yref.astype(np.float32)), (run.__name__, v)
+            assert dh[v] == oracle.dot_f64(x[lo:hi], p[lo:hi])[0], (run.__name__, v)
 
 
 def test_autotune_and_cache(api, tmp_path):

@@ -70,29 +70,35 @@ def test_dot_full_size_8_segments(api):
 
 
 @pytest.mark.parametrize("dtype,op", [(np.int64, "plus"), (np.int32, "plus"), (np.int64, "max"),
-                                      (np.int64, "min"), (np.float64, "plus"), (np.float32, "max")])
+                                      (np.int64, "min"), (np.int32, "mul"), (np.float64, "plus"),
+                                      (np.float32, "plus"), (np.float32, "max"), (np.float64, "min")])
 def test_reduce_ops_and_dtypes(api, dtype, op):
+    """Every operator and element type against the oracle's reduce: integers and
+    MIN / MAX exactly; float PLUS within the derived bound of the EXACT sum."""
+    import math
+    from fractions import Fraction
     n = 70_001
     lens = inputs.random_cut_segments(5, n, 5)
-    if np.issubdtype(dtype, np.integer):
+    if op == "mul":
+        x = inputs.uniform_int64(17, n, -1, 2).astype(dtype)       # products stay small: +-1, 0
+        x[x == 0] = 1
+    elif np.issubdtype(dtype, np.integer):
         x = inputs.uniform_int64(17, n, -1000, 1000).astype(dtype)
     else:
         x = inputs.uniform_pm1_f32(17, n).astype(dtype)
     vx = G.segvec(x, lens)
     out = torch.zeros(1, dtype=torch.from_numpy(x[:1]).dtype, device="cuda")
-    init = {"plus": 0, "max": -(10**6), "min": 10**6}[op]
+    init = {"plus": 3, "max": -(10**6), "min": 10**6, "mul": -1}[op]
     api.transform_reduce(vx, out, op=op, init=init)
     api.sync_status()
     got = out.item()
-    if op == "plus":
-        if np.issubdtype(dtype, np.integer):
-            assert got == oracle.segmented_reduce_alg3_i64(lens, x.astype(np.int64))
-        else:
-            s, a = oracle.inclusive_scan_f32_f64(x.astype(np.float32)) if dtype == np.float32 else (None, None)
-            exact = float(np.sum(x.astype(np.float64)))
-            assert abs(got - exact) <= 1e-12 * np.abs(x).sum() + 1e-9
+    exp = oracle.reduce(x, op, init=init)
+    if np.issubdtype(dtype, np.floating) and op == "plus":
+        esz = np.dtype(dtype).itemsize
+        scale = math.fsum(np.abs(x.astype(np.float64))) + abs(init)
+        err = abs(Fraction(got) - exp)
+        assert err <= Fraction(T.reduce_bound(n, scale, G.sms(), esz)), (got, float(exp))
     else:
-        exp = max(init, x.max()) if op == "max" else min(init, x.min())
         assert got == exp
 
 
@@ -105,7 +111,7 @@ def test_reduce_fused_transform_view(api):
     out = torch.zeros(1, dtype=torch.int64, device="cuda")
     api.transform_reduce(v, out)
     api.sync_status()
-    assert out.item() == int(((2 * xi + 1) ** 2).sum())
+    assert out.item() == oracle.reduce((2 * xi + 1) ** 2, "plus")
 
 
 def test_reduce_take_drop(api):
@@ -115,4 +121,12 @@ def test_reduce_take_drop(api):
     out = torch.zeros(1, dtype=torch.int64, device="cuda")
     api.transform_reduce(vx.view().drop(9_999).take(10_003), out)
     api.sync_status()
-    assert out.item() == int(xi[9_999:20_002].sum())
+    lens = [10_000, 10_000, 10_000]
+    kept = oracle.gather_segments(xi, lens, oracle.trim_segments(lens, 9_999, 9_999 + 10_003))
+    assert out.item() == oracle.reduce(kept, "plus")
+    # a scan over take / drop as well, into an output of another segmentation
+    o = G.empty_like_vec([3, 10_000], torch.int64)
+    api.inclusive_scan(vx.view().take(25_000).drop(14_997), o)
+    api.sync_status()
+    kept = oracle.gather_segments(xi, lens, oracle.trim_segments(lens, 14_997, 25_000))
+    assert np.array_equal(G.to_np(o), oracle.inclusive_scan_i64(kept))

@@ -90,7 +90,8 @@ def test_scan_i64_full_size_roofline_case(api):
     assert np.array_equal(got, oracle.inclusive_scan_i64(x))
 
 
-def check_f32_scan(got, x, lens, tile=4096):
+def check_f32_scan(got, x, lens, tile=None):
+    tile = tile or G.scan_tile(torch.float32)
     y, s = oracle.inclusive_scan_f32_f64(x)
     err = np.abs(got.astype(np.float64) - y)
     bound = T.scan_bound(s, G.tile_index(lens, tile))
@@ -120,7 +121,7 @@ def test_scan_f32_exact_special_cases(api):
     xi = inputs.uniform_int64(53, n, -8, 8).astype(np.float32)  # |prefix| < 2^24: exact
     api.inclusive_scan(G.segvec(xi, lens), out)
     api.sync_status()
-    assert np.array_equal(G.to_np(out), np.cumsum(xi.astype(np.int64)).astype(np.float32))
+    assert np.array_equal(G.to_np(out), oracle.inclusive_scan_i64(xi.astype(np.int64)).astype(np.float32))
 
 
 def test_scan_f32_full_size_8_segments(api):
@@ -140,6 +141,66 @@ def test_scan_f32_full_size_8_segments(api):
     print(f"scan f32 2^28: max |err|/S = {np.max(err / np.maximum(s, 1e-30)):.3e}; "
           f"max err {err.max():.3e} vs sequential fp32 {seq_err.max():.3e} "
           f"(ratio {err.max() / max(seq_err.max(), 1e-30):.3f})")
+    # the tree-shaped scan must not be less accurate than the naive sequential one
+    assert err.max() <= seq_err.max()
+
+
+# ---------------------------------------------------------------------------
+# fp32 at full size, exactly: integer-valued steps in {-1, 0, 1}.  Every partial
+# sum the kernel forms (in a thread, a warp, a tile, a lookback window, the
+# carry) is the sum of a contiguous range, i.e. a difference of two prefixes of
+# the walk; the test checks that the walk's prefixes span less than 2^24, so
+# every fp32 addition is exact and the result must equal the int64 oracle bit
+# for bit.  At 2^28 elements (32768 tiles over the persistent grid) this covers
+# every CTA's multi-tile lookahead and the fp32 lookback slots: a dropped,
+# doubled or misplaced tile carry anywhere changes the bits.
+# ---------------------------------------------------------------------------
+SEED_WALK = 2406 + 100
+
+
+@pytest.fixture(scope="module")
+def walk_2p28():
+    n = 1 << 28
+    xi = inputs.uniform_int64(SEED_WALK, n, -1, 2)
+    ref = oracle.inclusive_scan_i64(xi)
+    span = max(int(ref.max()), 0) - min(int(ref.min()), 0)
+    assert span < (1 << 24), span
+    return xi, ref
+
+
+def _walk_lens(kind, n):
+    if kind == "8_equal":
+        return inputs.block_segments(n, 8), inputs.block_segments(n, 8)
+    if kind == "1:2:3:2_into_8_equal":
+        return inputs.proportional_segments(n, [1, 2, 3, 2]), inputs.block_segments(n, 8)
+    cut = inputs.random_cut_segments(SEED_WALK + 1, n, 6)
+    lens = cut[:2] + [0] + cut[2:]                      # an empty segment in the middle
+    return lens, lens
+
+
+@pytest.mark.parametrize("kind", ["8_equal", "1:2:3:2_into_8_equal", "random_with_empty"])
+def test_scan_f32_full_size_exact_integer_walk(api, walk_2p28, kind):
+    xi, ref = walk_2p28
+    n = xi.size
+    lens, out_lens = _walk_lens(kind, n)
+    x = xi.astype(np.float32)
+    vx = G.segvec(x, lens)
+    out = G.empty_like_vec(out_lens, torch.float32)
+    api.inclusive_scan(vx, out)
+    api.sync_status()
+    got = G.to_np(out)
+    bad = np.flatnonzero(got != ref.astype(np.float32))
+    assert bad.size == 0, (bad[:5], got[bad[:5]], ref[bad[:5]])
+    if kind == "8_equal":
+        # the exclusive scan (init 0) and the reverse scan on the same walk, exactly
+        api.exclusive_scan(vx, out, init=0.0)
+        api.sync_status()
+        exp = oracle.scan(xi, "plus", exclusive=True, init=0)
+        assert np.array_equal(G.to_np(out), exp.astype(np.float32))
+        api.reverse_inclusive_scan(vx, out)
+        api.sync_status()
+        rev = oracle.reverse_inclusive_scan_f64(xi.astype(np.float64))
+        assert np.array_equal(G.to_np(out), rev.astype(np.float32))
 
 
 def test_exclusive_scan(api):
@@ -149,8 +210,7 @@ def test_exclusive_scan(api):
     out = G.empty_like_vec(lens, torch.int64)
     api.exclusive_scan(G.segvec(xi, lens), out, init=7)
     api.sync_status()
-    exp = np.concatenate([[7], 7 + oracle.inclusive_scan_i64(xi)[:-1]])
-    assert np.array_equal(G.to_np(out), exp)
+    assert np.array_equal(G.to_np(out), oracle.scan(xi, "plus", exclusive=True, init=7))
 
 
 @pytest.mark.parametrize("op", ["max", "min"])
@@ -161,8 +221,12 @@ def test_scan_max_min(api, op):
     out = G.empty_like_vec(lens, torch.float32)
     api.inclusive_scan(G.segvec(x, lens), out, op=op)
     api.sync_status()
-    f = np.maximum.accumulate if op == "max" else np.minimum.accumulate
-    assert np.array_equal(G.to_np(out), f(x))
+    assert np.array_equal(G.to_np(out), oracle.scan(x, op).astype(np.float32))
+    xi = inputs.uniform_int64(62, n, -10**15, 10**15)   # int64: both boundary-crossing and ragged
+    out64 = G.empty_like_vec(lens, torch.int64)
+    api.inclusive_scan(G.segvec(xi, lens), out64, op=op)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out64), oracle.scan(xi, op))
 
 
 def test_scan_over_fused_zip_transform(api):
@@ -186,7 +250,7 @@ def test_reverse_scan(api):
     api.sync_status()
     ref = oracle.reverse_inclusive_scan_f64(g.astype(np.float64))
     absref = oracle.reverse_inclusive_scan_f64(np.abs(g).astype(np.float64))
-    tiles_from_end = G.tile_index(lens, 4096)
+    tiles_from_end = G.tile_index(lens, G.scan_tile(torch.float32))
     tiles_from_end = tiles_from_end.max() - tiles_from_end
     err = np.abs(G.to_np(out).astype(np.float64) - ref)
     assert np.all(err <= T.scan_bound(absref, tiles_from_end))
@@ -194,7 +258,7 @@ def test_reverse_scan(api):
     out64 = G.empty_like_vec(lens, torch.int64)
     api.reverse_inclusive_scan(G.segvec(gi, lens), out64)
     api.sync_status()
-    assert np.array_equal(G.to_np(out64), np.cumsum(gi[::-1])[::-1])
+    assert np.array_equal(G.to_np(out64), oracle.reverse_inclusive_scan_f64(gi.astype(np.float64)).astype(np.int64))
 
 
 def test_bounded_wait_reports_timeout_and_recovers(api):
@@ -235,23 +299,14 @@ def test_exclusive_scan_max_min_plain_and_viewed(api, op, dt):
     init = 3
     api.exclusive_scan(G.segvec(x, lens), out, init=init, op=op)
     api.sync_status()
-    f = np.maximum if op == "max" else np.minimum
-    exp = np.empty(n, dt)
-    acc = dt(init)
-    for i in range(n):          # the definition: out_i = init op x_0 op ... op x_{i-1}
-        exp[i] = acc
-        acc = f(acc, x[i])
-    assert np.array_equal(G.to_np(out), exp)
-    # exclusive PLUS over view = transform(x, scale 2) | add 1
+    assert np.array_equal(G.to_np(out), oracle.scan(x, op, exclusive=True, init=init).astype(dt))
+    # exclusive PLUS over view = transform(x, scale 2) | add 1 (the view's values
+    # 2x + 1 are small integers in either type: exact)
     v = G.segvec(x, lens).view().transform("scale", 2).transform("add", 1)
     api.exclusive_scan(v, out, init=0)
     api.sync_status()
-    y = (2 * x.astype(np.int64) + 1) if dt == np.int32 else (2 * x + 1)
-    cs = np.concatenate([[0], np.cumsum(y)[:-1]])
-    if dt == np.int32:
-        assert np.array_equal(G.to_np(out).astype(np.int64), cs.astype(np.int32).astype(np.int64))
-    else:
-        assert np.array_equal(G.to_np(out), cs)   # small integers in fp64: exact
+    y = (2 * x.astype(np.int64) + 1).astype(dt)
+    assert np.array_equal(G.to_np(out), oracle.scan(y, "plus", exclusive=True, init=0).astype(dt))
 
 
 def test_scan_over_zip_view_float_within_bound(api):
@@ -269,7 +324,7 @@ def test_scan_over_zip_view_float_within_bound(api):
     ref = oracle.inclusive_scan_f64(prod)
     absref = oracle.inclusive_scan_f64(np.abs(prod))
     pieces = [4000, n // 3 - 4000, n - n // 3]
-    tiles = G.tile_index(pieces, 8192)
+    tiles = G.tile_index(pieces, G.scan_tile(torch.float32))
     # each product is rounded once to fp32 before the scan: one more rounding per term
     bound = T.scan_bound(absref, tiles) + 2.0 ** -24 * absref
     assert np.all(np.abs(G.to_np(out).astype(np.float64) - ref) <= bound)

@@ -136,18 +136,16 @@ def test_sort_repeated_calls_reuse_workspace(api):
         assert np.array_equal(G.to_np(out), oracle.sort(x))
 
 
-def test_sort_full_size_properties(api):
-    """The benchmark's workload (2^28 fp32 keys U[-1, 1) in 8 segments, the bench's
-    launch): non-decreasing, and the same multiset as the input (equal to an
-    independent library sort of the input)."""
+def test_sort_full_size_vs_oracle(api):
+    """The benchmark's workload (2^28 fp32 keys U[-1, 1) in 8 segments into 8
+    output segments, the bench's launch): bit-exact against the oracle's sort."""
     n = 1 << 28
-    dev = torch.device("cuda:0")
-    x = torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_SORT, n)).to(dev)
+    x = inputs.uniform_pm1_f32(inputs.SEED_SORT, n)
     lens = [n // 8] * 8
-    v = api.SegmentedVector.from_tensor(x, lens)
-    out = api.SegmentedVector.empty(lens, torch.float32, dev)
+    v = G.segvec(x, lens)
+    out = G.empty_like_vec(lens, torch.float32)
     api.sort(v, out)
     api.sync_status()
-    y = out.to_tensor()
-    assert bool((y[1:] >= y[:-1]).all())
-    assert torch.equal(y, torch.sort(x).values)
+    got = G.to_np(out)
+    exp = oracle.sort(x)
+    assert np.array_equal(got.view(np.uint32), exp.view(np.uint32))

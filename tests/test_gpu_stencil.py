@@ -22,9 +22,9 @@ def api():
 
 def run(api, u0, seg_rows, steps, wc=0.0, wn=0.25, transpose=False):
     u = torch.from_numpy(u0).cuda()
-    a = api.MdArray.from_tensor(u, seg_rows)
-    b = api.MdArray.empty(seg_rows, u0.shape[1])
-    t = api.MdArray.empty(seg_rows, u0.shape[1]) if steps > 1 else None
+    a = G.md_from(u, seg_rows)                  # guarded blocks, sentinel outer ghost rows
+    b = G.md_empty(seg_rows, u0.shape[1])
+    t = G.md_empty(seg_rows, u0.shape[1]) if steps > 1 else None
     (api.stencil5_T if transpose else api.stencil5)(a, b, t, steps, wc, wn)
     api.sync_status()
     return b.to_tensor().cpu().numpy()

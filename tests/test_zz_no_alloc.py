@@ -4,8 +4,10 @@ transform_reduce entry point and the oracle, through the C ABI.
 It exists for callers that cannot allocate device memory at the call (a
 framework owning all device memory through its pool, or a latency-critical loop
 that cannot pay for cudaMalloc / cudaFree): its scratch is a fixed device array
-of the library.  Two calls in a row must both be right, since every call reuses
-the array left by the previous one.  This file is collected last on purpose."""
+of the library.  It runs the same reduce kernel on the same grid as
+dr_transform_reduce, so the two results must be bit-identical.  Two calls in a
+row must both be right, since every call reuses the array left by the previous
+one.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -30,7 +32,8 @@ def _call(lib, vx, vy, lens, out, init=0.0):
                                   stream)
 
 
-def test_noalloc_dot_matches_transform_reduce_twice():
+@pytest.mark.parametrize("init", [0.0, 2.5])
+def test_noalloc_dot_matches_transform_reduce_twice(init):
     G.dev()
     from paper_2406_00158_gb300 import _lib as L
     from paper_2406_00158_gb300 import api
@@ -41,17 +44,32 @@ def test_noalloc_dot_matches_transform_reduce_twice():
     y = inputs.uniform_pm1_f32(inputs.SEED_DOT_Y, n)
     vx, vy = G.segvec(x, lens), G.segvec(y, lens)
     ref = torch.zeros(1, dtype=torch.float32, device="cuda")
-    api.transform_reduce(api.dot_view(vx, vy), ref)
+    api.transform_reduce(api.dot_view(vx, vy), ref, init=init)
     api.sync_status()
     d, ad = oracle.dot_f64(x, y)
-    tol = T.dot_bound(n, ad, G.sms())
+    tol = T.dot_bound(n, ad + abs(init), G.sms())
     for _ in range(2):
         out = torch.full((1,), float("nan"), dtype=torch.float32, device="cuda")
-        assert _call(lib, vx, vy, lens, out) == L.DR_OK, L.last_error()
+        assert _call(lib, vx, vy, lens, out, init) == L.DR_OK, L.last_error()
+        assert L.last_error() == ""
         api.sync_status()
         got = float(out.item())
-        assert abs(got - float(ref.item())) <= tol
-        assert abs(got - d) <= tol
+        assert got == float(ref.item())          # same kernel, same grid: same bits
+        assert abs(got - (d + init)) <= tol
+
+
+def test_noalloc_dot_all_segments_empty():
+    G.dev()
+    from paper_2406_00158_gb300 import _lib as L
+    from paper_2406_00158_gb300 import api
+    lib = L.lib()
+    lens = [0, 0, 0]
+    vx, vy = G.segvec(np.zeros(0, np.float32), lens), G.segvec(np.zeros(0, np.float32), lens)
+    for _ in range(2):
+        out = torch.full((1,), float("nan"), dtype=torch.float32, device="cuda")
+        assert _call(lib, vx, vy, lens, out, 1.75) == L.DR_OK, L.last_error()
+        api.sync_status()
+        assert float(out.item()) == 1.75         # the empty sum is init
 
 
 def test_noalloc_dot_rejects_too_many_segments():

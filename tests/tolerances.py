@@ -3,11 +3,14 @@ summation trees (standard results for recursive / blocked summation: a sum of
 terms whose longest chain of dependent roundings has k adds has error at most
 gamma_k * sum|terms|, gamma_k = k u / (1 - k u), u = 2^-24 for fp32).
 
-dot (transform_reduce over zip | multiply): every thread accumulates V=4
-independent FMA chains over its tiles (RCH=4 terms per tile per chain), then
-the 4 chains (2 levels), a warp (5 levels), the block's 8 warps (3 levels),
-and the last CTA folds the grid's partials (ceil(grid/256) sequential, then 8
-tree levels), plus init.
+reduce / dot (transform_reduce over zip | multiply): every thread keeps
+V = 16 / sizeof(T) independent accumulation chains (one per lane of a 16-byte
+vector), each taking RCH = 4 terms per tile (one FMA or add each) over the
+tiles its CTA strides over; the V chains are then combined one after the
+other (V - 1 roundings), then a warp (5 levels), the block's 8 warps (3
+levels), and the last CTA folds the grid's partials (ceil(grid/256)
+sequential, then 5 + 3 tree levels), plus init.  The grid is fixed: CTAs per
+SM x SMs (capped at the tile count).
 
 scan: inside a tile an element's prefix takes at most 3 (thread) + 5 (warp)
 + 5 (block) + 3 (offset combine) roundings; across tiles the carry is a chain
@@ -17,21 +20,37 @@ aggregate) roundings of partial sums bounded by the prefix's |x| sum.
 import math
 
 U32 = 2.0 ** -24
+U64 = 2.0 ** -53
 
 
 def gamma(k: int, u: float = U32) -> float:
     return k * u / (1.0 - k * u)
 
 
-def dot_chain(n: int, sms: int, tile: int = 4096, ctas_per_sm: int = 4, threads: int = 256) -> int:
-    grid = sms * ctas_per_sm
+def reduce_chain(n: int, sms: int, esize: int = 4, ctas_per_sm: int = 4, threads: int = 256,
+                 rch: int = 4) -> int:
+    """Longest chain of dependent roundings in the reduce kernel's tree."""
+    v = 16 // esize
+    tile = threads * rch * v
     ntiles = max(1, -(-n // tile))
+    grid = min(sms * ctas_per_sm, ntiles)
     per_cta = -(-ntiles // grid)
-    return per_cta * 4 + 2 + 5 + 3 + (-(-grid // threads)) + 5 + 3 + 1
+    return per_cta * rch + (v - 1) + 5 + 3 + (-(-grid // threads)) + 5 + 3 + 1
+
+
+def dot_chain(n: int, sms: int) -> int:
+    return reduce_chain(n, sms, 4)
 
 
 def dot_bound(n: int, abs_sum: float, sms: int) -> float:
     return gamma(dot_chain(n, sms)) * abs_sum
+
+
+def reduce_bound(n: int, abs_sum: float, sms: int, esize: int) -> float:
+    """|computed - exact| for a PLUS reduce of n elements of a float type of
+    esize bytes (u = 2^-24 for fp32, 2^-53 for fp64), scaled by sum |x|."""
+    u = U32 if esize == 4 else U64
+    return gamma(reduce_chain(n, sms, esize), u) * abs_sum
 
 
 def scan_bound(abs_prefix, tile_of_elem):
