@@ -11,8 +11,10 @@ reported under "rows".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank runs the same workload on its own GPU (independent
-problems: weak scaling, no data-path collective); rank 0 prints one JSON line.
+Under torchrun the one 2^28 range is sharded over the ranks (segment k of 8 on
+rank k*N//8; strong scaling): the dot all-gathers the per-rank partials, the scan
+all-gathers the run totals and starts each rank's local scan from its carry
+(NCCL); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -180,7 +182,7 @@ def run_reference(args) -> None:
     line = {
         "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded SplitMix64, U[-1,1))",
         "config": {"workload": WORKLOAD, "sample": f"n=2^26 of the 2^28 workload per step",
                    "parallelism": "CPU oracle, 1 thread"},
@@ -395,6 +397,87 @@ def measure_rows(api, dev, s, peak) -> dict:
 
 
 # ------------------------------------------------------------------------------------------
+# the headline step: one GPU, or the one range sharded over the ranks
+# ------------------------------------------------------------------------------------------
+class Headline:
+    """dot + inclusive_scan of the 2^28 fp32 range in 8 segments.  One rank: the
+    single-range kernels on persistent views.  N ranks: segment k lives on rank
+    k*N//8 and the step is the sharded dot and scan (paper_2406_00158_gb300.shard):
+    per rank 2 + 3 of the library's launches plus two NCCL all-gathers."""
+
+    def __init__(self, api, D, dev, s, x, y):
+        import torch
+        self.api, self.s, self.D, self.torch = api, s, D, torch
+        self.x, self.y = x, y
+        lens = inputs.block_segments(N_ELEMS, NSEG)
+        starts = np.concatenate([[0], np.cumsum(lens)])
+        self.dotbuf = torch.zeros(1, dtype=torch.float32, device=dev)
+        if D.world == 1:
+            self.vx = api.SegmentedVector.from_tensor(torch.from_numpy(x).to(dev), lens)
+            self.vy = api.SegmentedVector.from_tensor(torch.from_numpy(y).to(dev), lens)
+            self.out = api.SegmentedVector.empty(lens, torch.float32, dev)
+            self.dview = api.dot_view(self.vx, self.vy)
+            self.xview = self.vx.view()
+            self.ranges = [(0, N_ELEMS)]
+            self.local_elems = N_ELEMS
+            self.launches_per_step = 2
+            self.sharded = False
+        else:
+            from paper_2406_00158_gb300 import shard
+            self.shard = shard
+            comm = shard.TorchComm()
+            owners = shard.block_owners(NSEG, D.world)
+            mine = [k for k in range(NSEG) if owners[k] == D.rank]
+            seg = lambda a, k: torch.from_numpy(a[starts[k]:starts[k + 1]]).to(dev)
+            self.X = shard.ShardedVector(comm, lens, owners, [seg(x, k) for k in mine])
+            self.Y = shard.ShardedVector(comm, lens, owners, [seg(y, k) for k in mine])
+            self.O = shard.ShardedVector.empty_like(self.X)
+            self.ranges = [(int(starts[k]), int(starts[k + 1])) for k in mine]
+            self.local_elems = sum(b - a for a, b in self.ranges)
+            self.launches_per_step = 5
+            self.sharded = True
+
+    def dot(self):
+        if self.sharded:
+            self.shard.dot(self.X, self.Y, self.dotbuf)
+        else:
+            self.api.transform_reduce(self.dview, self.dotbuf, stream=self.s)
+
+    def scan(self):
+        if self.sharded:
+            self.shard.scan(self.X, self.O)
+        else:
+            self.api.inclusive_scan(self.xview, self.out, stream=self.s)
+
+    def step(self):
+        self.dot()
+        self.scan()
+
+    def pin_host(self):
+        t = self.torch
+        self.hx = [t.from_numpy(self.x[a:b]).pin_memory() for a, b in self.ranges]
+        self.hy = [t.from_numpy(self.y[a:b]).pin_memory() for a, b in self.ranges]
+        self.hout = [t.empty(b - a, dtype=t.float32).pin_memory() for a, b in self.ranges]
+        self.hdot = t.empty(1, dtype=t.float32).pin_memory()
+
+    def e2e_step(self):
+        """This rank's inputs from pinned host memory, the step, its results back."""
+        if self.sharded:
+            for k, hx, hy in zip(self.X.mine, self.hx, self.hy):
+                self.X.seg[k].copy_(hx, non_blocking=True)
+                self.Y.seg[k].copy_(hy, non_blocking=True)
+            self.step()
+            for k, ho in zip(self.O.mine, self.hout):
+                ho.copy_(self.O.seg[k], non_blocking=True)
+        else:
+            self.vx.copy_from_host(self.hx[0], self.s)
+            self.vy.copy_from_host(self.hy[0], self.s)
+            self.step()
+            self.out.copy_to_host(self.hout[0], self.s)
+        self.hdot.copy_(self.dotbuf, non_blocking=True)
+
+
+# ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
 def main() -> None:
@@ -530,26 +613,17 @@ def main() -> None:
     dev = torch.device("cuda", D.local)
     s = torch.cuda.current_stream()
 
-    # ---- inputs: x, y fp32 U[-1,1), 8 equal segments, one allocation each
+    # ---- inputs: x, y fp32 U[-1,1), 8 equal segments, one allocation each; with N > 1
+    # ranks the segments are sharded over the GPUs (segment k on rank k*N//8) and the
+    # one 2^28 range is strong-scaled
     x = inputs.uniform_pm1_f32(inputs.SEED_DOT_X, N_ELEMS)
     y = inputs.uniform_pm1_f32(inputs.SEED_DOT_Y, N_ELEMS)
-    lens = inputs.block_segments(N_ELEMS, NSEG)
-    vx = api.SegmentedVector.from_tensor(torch.from_numpy(x).to(dev), lens)
-    vy = api.SegmentedVector.from_tensor(torch.from_numpy(y).to(dev), lens)
-    out = api.SegmentedVector.empty(lens, torch.float32, dev)
-    dot = torch.zeros(1, dtype=torch.float32, device=dev)
-    dview = api.dot_view(vx, vy)
-    xview = vx.view()
-
-    def step():
-        api.transform_reduce(dview, dot, stream=s)
-        api.inclusive_scan(xview, out, stream=s)
-
+    H = Headline(api, D, dev, s, x, y)
     for _ in range(args.warmup):
-        step()
+        H.step()
     api.sync_status(s)
 
-    # ---- timed region: K steps, events around each kernel on the launching stream
+    # ---- timed region: K steps, events around each part on the launching stream
     K = args.steps
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
     clocks = ClockSampler(gpu_index_for_smi(D.local))
@@ -562,9 +636,9 @@ def main() -> None:
     t0.record(s)
     ev[0].record(s)
     for k in range(K):
-        api.transform_reduce(dview, dot, stream=s)
+        H.dot()
         ev[2 * k + 1].record(s)
-        api.inclusive_scan(xview, out, stream=s)
+        H.scan()
         ev[2 * k + 2].record(s)
     t1.record(s)
     torch.cuda.synchronize()
@@ -575,50 +649,39 @@ def main() -> None:
     ms = D.max(ms_local)
     dot_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(K)]
     scan_ms = [ev[2 * k + 1].elapsed_time(ev[2 * k + 2]) for k in range(K)]
-    bytes_step = N_ELEMS * (BYTES_DOT + BYTES_SCAN)
-    value = D.sum(bytes_step * K) / (ms / 1e3) / 1e9
+    bytes_step = N_ELEMS * (BYTES_DOT + BYTES_SCAN)          # the whole range, all ranks together
+    value = bytes_step * K / (ms / 1e3) / 1e9
 
     peak, peak_kind = peaks()
     kern = {
-        "dot": (statistics.mean(dot_ms), N_ELEMS * BYTES_DOT),
-        "scan": (statistics.mean(scan_ms), N_ELEMS * BYTES_SCAN),
+        "dot": (statistics.mean(dot_ms), H.local_elems * BYTES_DOT),
+        "scan": (statistics.mean(scan_ms), H.local_elems * BYTES_SCAN),
     }
     dom = max(kern, key=lambda k: kern[k][0])
     dom_ms, dom_bytes = kern[dom]
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
+    if os.path.exists(tr_path) and D.world == 1:
         traffic = json.load(open(tr_path)).get(dom)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e_val = None
     if not args.no_e2e:
-        hx = torch.from_numpy(x).pin_memory()
-        hy = torch.from_numpy(y).pin_memory()
-        hout = torch.empty(N_ELEMS, dtype=torch.float32).pin_memory()
-        hdot = torch.empty(1, dtype=torch.float32).pin_memory()
+        H.pin_host()
         e2e_steps = max(3, min(10, K))
-
-        def e2e_step():
-            vx.copy_from_host(hx, s)
-            vy.copy_from_host(hy, s)
-            step()
-            out.copy_to_host(hout, s)
-            hdot.copy_(dot, non_blocking=True)
-
-        e2e_step()
+        H.e2e_step()
         torch.cuda.synchronize()
         D.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s)
         for _ in range(e2e_steps):
-            e2e_step()
+            H.e2e_step()
         e1.record(s)
         torch.cuda.synchronize()
         e2e_ms = D.max(e0.elapsed_time(e1))
-        e2e_val = D.sum(bytes_step * e2e_steps) / (e2e_ms / 1e3) / 1e9
+        e2e_val = bytes_step * e2e_steps / (e2e_ms / 1e3) / 1e9
         api.sync_status(s)
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample (rank 0, N = 1)
@@ -632,17 +695,19 @@ def main() -> None:
                "host": {"machine": platform.machine(), "logical_cpus": os.cpu_count()}}
 
     rows = {}
-    if not args.no_rows:
+    if not args.no_rows and D.world == 1:      # the other rows are single-GPU workloads
         rows = measure_rows(api, dev, s, peak)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": D.world, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded SplitMix64, U[-1,1))",
         "config": {"workload": WORKLOAD if args.log2n == 28 else WORKLOAD.replace("2^28", f"2^{args.log2n}"),
                    "n": N_ELEMS, "segments": NSEG,
                    "l2": "no flush: 3 GiB touched per step > 129 MB L2",
-                   "parallelism": f"independent replicas x{D.world}" if D.world > 1 else "1 GPU"},
+                   "parallelism": (f"one range sharded over {D.world} GPUs: segment k on rank k*{D.world}//8; "
+                                   "dot: all-gather of partials; scan: all-gather of run totals + carry-in")
+                   if D.world > 1 else "1 GPU"},
         "frac_of_peak": value / D.world / peak,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
@@ -653,8 +718,8 @@ def main() -> None:
                    "sms": torch.cuda.get_device_properties(dev).multi_processor_count,
                    "l2_bytes": torch.cuda.get_device_properties(dev).L2_cache_size},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": 2 * N_ELEMS * 4,
-                "d2h_bytes_per_step": N_ELEMS * 4 + 4} if e2e_val is not None else None,
-        "gpu_launches": 2 * K,
+                "d2h_bytes_per_step": N_ELEMS * 4 + 4 * D.world} if e2e_val is not None else None,
+        "gpu_launches": H.launches_per_step * K,
         "cpu_baseline": cpu,
         "rows": rows,
     }

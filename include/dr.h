@@ -263,6 +263,19 @@ int dr_inclusive_scan(const dr_view* in, dr_vec* out, int op, dr_stream_t stream
 int dr_exclusive_scan(const dr_view* in, dr_vec* out, int op, const void* init,
                       dr_stream_t stream);
 
+/* Scan with a carry-in read from device memory.  Algorithm 4 (Sec. 4.3) adds
+ * to each segment the total of everything before it; when the segments before
+ * this range live on other GPUs (a range sharded over ranks), that total
+ * arrives as a device value, e.g. from a collective, and is passed here
+ * without a host round trip.  op in {PLUS, MIN, MAX}.
+ *   exclusive == 0: out_i = carry op in_0 op ... op in_i
+ *   exclusive != 0: out_0 = carry, out_i = carry op in_0 op ... op in_{i-1}
+ * dev_carry: one element of the view's dtype in device memory, aligned to its
+ * size, read by the kernel (so earlier work on `stream` may produce it).
+ * Otherwise as dr_inclusive_scan (same kernel, same workspace rules). */
+int dr_scan_with_carry(const dr_view* in, dr_vec* out, int op, int exclusive, const void* dev_carry,
+                       dr_stream_t stream);
+
 /* Reverse inclusive scan: out_j = in_j + in_{j+1} + ... + in_{n-1}.  This is
  * the adjoint of the PLUS inclusive scan (gradient of y = scan(x) is
  * x_bar = reverse_scan(y_bar)). */
@@ -368,6 +381,28 @@ int dr_scale_by_partner(const dr_vec* x, const dr_vec* y, const float* dev_g, dr
  * into the neighbours' ghost rows of its output.  in, out, tmp distinct. */
 int dr_stencil5(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
                 dr_stream_t stream);
+
+/* Marks a row-block array as one rank's share of a taller grid split by rows
+ * over several GPUs (Sec. 4.2.2's block_row partition with blocks on
+ * different memory locales): with top (bottom) != 0 the first block's top
+ * (the last block's bottom) ghost row holds the row just above (below) the
+ * share -- written by the caller before each step, e.g. received from the
+ * neighbouring rank -- and the stencil reads it instead of the zero outside the
+ * grid.  Default: both 0 (the array is the whole grid).  Such an array is
+ * stepped one step per call (the caller exchanges the outer rows in between);
+ * in and out of a call must agree on these flags.  Host only. */
+int dr_md2_set_external_halos(dr_md2* m, int top, int bottom);
+
+/* One step of dr_stencil5 restricted to a part of the row blocks (64 rows
+ * each, per block), so that an exchange of the outer ghost rows can overlap
+ * the update of the rows that do not read them:
+ *   DR_ROWS_ALL   every row block (= dr_stencil5 with steps == 1);
+ *   DR_ROWS_INNER all but the array's first and last row block;
+ *   DR_ROWS_OUTER the first and the last row block (the only ones that read
+ *                 the outer ghost rows).
+ * INNER then OUTER (or OUTER then INNER) on one stream is one full step. */
+enum dr_rows_part { DR_ROWS_ALL = 0, DR_ROWS_INNER = 1, DR_ROWS_OUTER = 2 };
+int dr_stencil5_part(dr_md2* in, dr_md2* out, int part, double wc, double wn, dr_stream_t stream);
 
 /* The transposed operator A^T applied `steps` times (adjoint of dr_stencil5
  * for the gradient w.r.t. the initial state).  With a zero ghost ring the

@@ -11,8 +11,8 @@ generator) imports without torch or the CUDA library.
 """
 import importlib
 
-_API = ("SegmentedVector", "View", "MdArray", "Batch", "inclusive_scan", "exclusive_scan",
-        "reverse_inclusive_scan", "transform_reduce", "scale_by_partner", "stencil5", "stencil5_T", "stencil5_T_wgrad",
+_API = ("SegmentedVector", "View", "MdArray", "Batch", "inclusive_scan", "exclusive_scan", "scan_with_carry",
+        "reverse_inclusive_scan", "transform_reduce", "scale_by_partner", "stencil5", "stencil5_part", "stencil5_T", "stencil5_T_wgrad",
         "sync_status", "set_spin_limit", "debug_skip_publish", "block_lengths", "dot_view", "stream_handle",
         "for_each", "transform", "FOR_EACH_FNS", "sort")
 

@@ -27,6 +27,8 @@ DR_U_SCALE, DR_U_ADD, DR_U_NEG, DR_U_ABS, DR_U_SQUARE = range(5)
 # enum dr_kernel_family
 DR_K_SCAN, DR_K_REDUCE, DR_K_FOREACH, DR_K_SORT = range(4)
 DR_ZIP_STRICT_ALIGN = 1
+# enum dr_rows_part
+DR_ROWS_ALL, DR_ROWS_INNER, DR_ROWS_OUTER = range(3)
 
 
 class dr_piece(ctypes.Structure):
@@ -85,6 +87,7 @@ PROTOTYPES = {
     "dr_view_segments": (_I, [_P, _I, ctypes.POINTER(dr_piece)]),
     "dr_inclusive_scan": (_I, [_P, _P, _I, _P]),
     "dr_exclusive_scan": (_I, [_P, _P, _I, _P, _P]),
+    "dr_scan_with_carry": (_I, [_P, _P, _I, _I, _P, _P]),
     "dr_reverse_inclusive_scan": (_I, [_P, _P, _P]),
     "dr_transform_reduce": (_I, [_P, _I, _P, _P, _P]),
     "dr_scale_by_partner": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -93,6 +96,8 @@ PROTOTYPES = {
     "dr_sort": (_I, [_P, _P, _P]),
     "dr_dot_f32_noalloc": (_I, [_I, _PI64, _PP, _PP, ctypes.c_float, _P, _P]),
     "dr_stencil5": (_I, [_P, _P, _P, _I, _D, _D, _P]),
+    "dr_stencil5_part": (_I, [_P, _P, _I, _D, _D, _P]),
+    "dr_md2_set_external_halos": (_I, [_P, _I, _I]),
     "dr_stencil5_T": (_I, [_P, _P, _P, _I, _D, _D, _P]),
     "dr_stencil5_T_wgrad": (_I, [_P, _P, _P, _D, _D, _P, _P]),
     "dr_batch_plan": (_I, [_I, _PP, _PP, _PP, _P, ctypes.POINTER(dr_tune), _PP]),

@@ -265,6 +265,18 @@ def exclusive_scan(inp, out: SegmentedVector, init, op="plus", stream=None) -> S
     return out
 
 
+def scan_with_carry(inp, out: SegmentedVector, carry: torch.Tensor, op="plus", exclusive: bool = False,
+                    stream=None) -> SegmentedVector:
+    """Scan whose chain starts from a device value: inclusive out_i = carry op
+    in_0 op ... op in_i; exclusive out_0 = carry, ... (carry: a 1-element device
+    tensor of the vector's dtype)."""
+    v = _as_view(inp)
+    assert carry.is_cuda and carry.dtype == out.dtype and carry.numel() >= 1
+    call("dr_scan_with_carry", v.handle, out.handle, _op(op), 1 if exclusive else 0,
+         ctypes.c_void_p(carry.data_ptr()), stream_handle(stream))
+    return out
+
+
 def reverse_inclusive_scan(inp, out: SegmentedVector, stream=None) -> SegmentedVector:
     v = _as_view(inp)
     call("dr_reverse_inclusive_scan", v.handle, out.handle, stream_handle(stream))
@@ -355,6 +367,12 @@ class MdArray:
     def exchange_halos(self, stream=None) -> None:
         call("dr_md2_exchange_halos", self.handle, stream_handle(stream))
 
+    def set_external_halos(self, top: bool, bottom: bool) -> None:
+        """This array is one rank's share of a taller grid: its outer ghost rows
+        hold the neighbouring shares' rows (written by the caller)."""
+        call("dr_md2_set_external_halos", self.handle, 1 if top else 0, 1 if bottom else 0)
+        self.ext = (bool(top), bool(bottom))
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h and L._lib is not None:
@@ -364,6 +382,17 @@ class MdArray:
 def stencil5(inp: MdArray, out: MdArray, tmp: Optional[MdArray], steps: int, wc: float = 0.0,
              wn: float = 0.25, stream=None) -> MdArray:
     call("dr_stencil5", inp.handle, out.handle, tmp.handle if tmp is not None else None, int(steps),
+         float(wc), float(wn), stream_handle(stream))
+    return out
+
+
+ROWS = {"all": L.DR_ROWS_ALL, "inner": L.DR_ROWS_INNER, "outer": L.DR_ROWS_OUTER}
+
+
+def stencil5_part(inp: MdArray, out: MdArray, part="all", wc: float = 0.0, wn: float = 0.25,
+                  stream=None) -> MdArray:
+    """One stencil step over the inner or outer row blocks only (see dr.h)."""
+    call("dr_stencil5_part", inp.handle, out.handle, ROWS[part] if isinstance(part, str) else int(part),
          float(wc), float(wn), stream_handle(stream))
     return out
 

@@ -722,7 +722,7 @@ static int check_single(const dr_view* in, const char* who) {
 }
 
 static int do_scan(const char* who, const dr_view* in_c, dr_vec* out, int op, bool reverse, bool exclusive,
-                   const void* init, cudaStream_t s) {
+                   const void* init, cudaStream_t s, const void* dev_carry = nullptr) {
   clear_error();
   if (int r = check_single(in_c, who)) return r;
   dr_view* in = const_cast<dr_view*>(in_c);
@@ -731,7 +731,9 @@ static int do_scan(const char* who, const dr_view* in_c, dr_vec* out, int op, bo
   if (out->n < in->size)
     return fail(DR_E_INVAL, "%s: output has %lld elements, input %lld", who, (long long)out->n, (long long)in->size);
   if (op != DR_PLUS && op != DR_MIN && op != DR_MAX) return fail(DR_E_INVAL, "%s: op must be PLUS, MIN or MAX", who);
-  if (exclusive && !init) return fail(DR_E_INVAL, "%s: NULL init", who);
+  if (exclusive && !init && !dev_carry) return fail(DR_E_INVAL, "%s: NULL init", who);
+  if (dev_carry && (uintptr_t)dev_carry % esize(in->dtype))
+    return fail(DR_E_ALIGN, "%s: carry pointer not aligned to the element size", who);
   if (in->size == 0) return DR_OK;
   static thread_local ScanParams p;
   std::memset(&p, 0, sizeof p);
@@ -746,7 +748,8 @@ static int do_scan(const char* who, const dr_view* in_c, dr_vec* out, int op, bo
   if (!p.status) return fail(DR_E_CUDA, "%s: no device status word", who);
   p.spin_limit = spin_limit();
   p.skip_tile = take_skip_publish();
-  if (exclusive) std::memcpy(&p.init_bits, init, esize(in->dtype));
+  if (exclusive && init) std::memcpy(&p.init_bits, init, esize(in->dtype));
+  p.carry = dev_carry;
   cudaError_t e = launch_scan(p, reverse, scan_grid(in->dtype, p.ntiles), s);
   in->ws_scan.mark(s);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
@@ -758,6 +761,15 @@ extern "C" int dr_inclusive_scan(const dr_view* in, dr_vec* out, int op, dr_stre
 
 extern "C" int dr_exclusive_scan(const dr_view* in, dr_vec* out, int op, const void* init, dr_stream_t stream) {
   return do_scan("dr_exclusive_scan", in, out, op, false, true, init, (cudaStream_t)stream);
+}
+
+extern "C" int dr_scan_with_carry(const dr_view* in, dr_vec* out, int op, int exclusive, const void* dev_carry,
+                                  dr_stream_t stream) {
+  if (!dev_carry) {
+    clear_error();
+    return fail(DR_E_INVAL, "dr_scan_with_carry: NULL carry");
+  }
+  return do_scan("dr_scan_with_carry", in, out, op, false, exclusive != 0, nullptr, (cudaStream_t)stream, dev_carry);
 }
 
 extern "C" int dr_reverse_inclusive_scan(const dr_view* in, dr_vec* out, dr_stream_t stream) {
@@ -982,10 +994,16 @@ extern "C" int dr_sort(const dr_view* in_c, dr_vec* out, dr_stream_t stream) {
 }
 
 static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
-                      cudaStream_t s, const dr_md2* prev = nullptr, double* acc = nullptr) {
+                      cudaStream_t s, const dr_md2* prev = nullptr, double* acc = nullptr, int part = DR_ROWS_ALL) {
   clear_error();
   if (!in || !out) return fail(DR_E_INVAL, "%s: NULL array", who);
   if (steps < 1) return fail(DR_E_INVAL, "%s: steps must be >= 1", who);
+  if (part < DR_ROWS_ALL || part > DR_ROWS_OUTER) return fail(DR_E_INVAL, "%s: unknown row part %d", who, part);
+  if (steps > 1 && (in->ext_top || in->ext_bot))
+    return fail(DR_E_INVAL, "%s: an array with external halos needs an exchange between steps: one step per call",
+                who);
+  if (out->ext_top != in->ext_top || out->ext_bot != in->ext_bot)
+    return fail(DR_E_INVAL, "%s: in and out differ in their external halos", who);
   if (steps > 1 && !tmp) return fail(DR_E_INVAL, "%s: tmp is required when steps > 1", who);
   auto same = [&](const dr_md2* m) {
     return m->rows == in->rows && m->cols == in->cols && m->srows == in->srows;
@@ -1014,6 +1032,8 @@ static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int
     p.nseg = nseg;
     p.cols = in->cols;
     p.nrb = nrb;
+    p.ext_top = in->ext_top;
+    p.ext_bot = in->ext_bot;
     p.wc = (float)wc;
     p.wn = (float)wn;
     p.vec_ok = vec ? 1 : 0;
@@ -1031,7 +1051,17 @@ static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int
       g.rb_begin = rb;
       rb += (in->srows[k] + kStencilRowsPerCta - 1) / kStencilRowsPerCta;
     }
-    cudaError_t e = launch_stencil(p, s);
+    // ALL: every row block; OUTER: the first and the last row block (the only ones
+    // that read the outer ghost rows); INNER: the others
+    int64_t nlaunch = nrb;
+    if (part == DR_ROWS_OUTER) {
+      p.outer_only = 1;
+      nlaunch = nrb > 1 ? 2 : 1;
+    } else if (part == DR_ROWS_INNER) {
+      p.rb_lo = 1;
+      nlaunch = nrb > 2 ? nrb - 2 : 0;
+    }
+    cudaError_t e = launch_stencil(p, nlaunch, s);
     if (e != cudaSuccess) return cuda_fail(e, who);
     src = dst;
   }
@@ -1041,6 +1071,18 @@ static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int
 extern "C" int dr_stencil5(dr_md2* in, dr_md2* out, dr_md2* tmp, int steps, double wc, double wn,
                            dr_stream_t stream) {
   return do_stencil("dr_stencil5", in, out, tmp, steps, wc, wn, (cudaStream_t)stream);
+}
+
+extern "C" int dr_stencil5_part(dr_md2* in, dr_md2* out, int part, double wc, double wn, dr_stream_t stream) {
+  return do_stencil("dr_stencil5_part", in, out, nullptr, 1, wc, wn, (cudaStream_t)stream, nullptr, nullptr, part);
+}
+
+extern "C" int dr_md2_set_external_halos(dr_md2* m, int top, int bottom) {
+  clear_error();
+  if (!m) return fail(DR_E_INVAL, "dr_md2_set_external_halos: NULL array");
+  m->ext_top = top ? 1 : 0;
+  m->ext_bot = bottom ? 1 : 0;
+  return DR_OK;
 }
 
 // A^T of the zero-ghost-ring 5-point operator: column (k,l) of A^T is row (k,l)

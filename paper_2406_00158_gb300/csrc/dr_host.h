@@ -88,6 +88,9 @@ struct dr_md2 {
   int64_t rows = 0, cols = 0;
   std::vector<char*> ptr;
   std::vector<int64_t> srows;
+  // the array is one rank's share of a taller grid: its outer ghost rows hold
+  // the neighbouring shares' boundary rows (filled by the caller) instead of zero
+  int ext_top = 0, ext_bot = 0;
 };
 
 struct dr_view {

@@ -84,6 +84,7 @@ struct ScanParams {
   int64_t spin_limit;
   int64_t skip_tile;  // test hook: this logical tile never publishes (-1: none)
   unsigned long long init_bits;
+  const void* carry;  // device carry-in (one element) or NULL; forward scans only
   KPiece pc[kMaxPieces];
 };
 
@@ -178,6 +179,10 @@ struct StencilParams {
   int nseg;
   int64_t cols;
   int64_t nrb;       // total row blocks
+  int64_t rb_lo;     // first row block of this launch (grid.y row blocks from there)
+  int outer_only;    // 1: grid.y = 1 or 2 row blocks, the first and the last
+  int ext_top;       // 1: the first block's top ghost row holds real data (a neighbour's row)
+  int ext_bot;       // 1: the last block's bottom ghost row holds real data
   float wc, wn;
   int vec_ok;        // cols % 4 == 0 and all pointers 16-byte aligned
   double* acc;       // weight-gradient step only: acc[0] += <in, prev>, acc[1] += <N(in), prev>
@@ -215,7 +220,7 @@ size_t scan_ws_bytes(int64_t ntiles, int dtype);
 cudaError_t launch_reduce(const ReduceParams& p, int grid, cudaStream_t s);
 cudaError_t launch_scan(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
 cudaError_t launch_scale(const ScaleParams& p, int grid, cudaStream_t s);
-cudaError_t launch_stencil(const StencilParams& p, cudaStream_t s);
+cudaError_t launch_stencil(const StencilParams& p, int64_t nrb_launch, cudaStream_t s);
 cudaError_t launch_halo(const HaloParams& p, cudaStream_t s);
 cudaError_t launch_for_each(const ForEachParams& p, cudaStream_t s);
 cudaError_t launch_transform(const TransformParams& p, cudaStream_t s);

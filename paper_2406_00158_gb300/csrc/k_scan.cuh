@@ -256,6 +256,14 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
   const T ident = O::template identity<T>();
   const unsigned long long keep = l2_policy_evict_last(), drop = l2_policy_evict_first();
   (void)keep;
+  // Carry-in from device memory (e.g. the total of the part of the range held by
+  // lower-ranked GPUs): an inclusive scan's chain starts from it, an exclusive
+  // scan takes it as its initial value.
+  T chain0 = ident, init = from_bits<T>(P.init_bits);
+  if (P.carry) {
+    if constexpr (EXCL) init = *reinterpret_cast<const T*>(P.carry);
+    else if constexpr (!REV) chain0 = *reinterpret_cast<const T*>(P.carry);
+  }
 
   // prologue: tickets of the first kStages tiles (in order) and their loads
   if (tid == 0) {
@@ -323,12 +331,13 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
       break;
     }
 
-    T prefix = ident;
+    T prefix = (haveS && tprev == 0) ? chain0 : ident;
     if (warp == 0) {
       if (haveR) {
         T loc[SR], exc;
         const T agg = block_totals<T, OP>(s_totR, lane, loc, exc);
-        if (lane == 0 && t != P.skip_tile) slots.publish(t, tag, t == 0 ? kStateP : kStateA, agg);
+        if (lane == 0 && t != P.skip_tile)
+          slots.publish(t, tag, t == 0 ? kStateP : kStateA, t == 0 ? O::apply(chain0, agg) : agg);
         if (lane == 0) s_agg = agg;
       }
       // ---- S phase carry: lookback for tprev
@@ -359,7 +368,6 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
         }
       }
       __syncthreads();
-      const T init = from_bits<T>(P.init_bits);
 #pragma unroll
       for (int c = 0; c < SCH; ++c) {
         const int q = REV ? SQ - 1 - (c * SNW + warp) : c * SNW + warp;

@@ -88,15 +88,17 @@ __device__ __forceinline__ float upd(float n, float s, float w, float e, float c
 // <u_bar, N u> = <N u_bar, u> because N is symmetric) into acc[0], acc[1].
 template <int VW, bool WGRAD>
 __global__ void __launch_bounds__(TX, DR_STENCIL_MINB) k_stencil5(const __grid_constant__ StencilParams P) {
-  const int s = find_seg(P, blockIdx.y);
+  const int64_t rb = P.outer_only ? (blockIdx.y == 0 ? 0 : P.nrb - 1) : P.rb_lo + (int64_t)blockIdx.y;
+  const int s = find_seg(P, rb);
   const StencilSeg& S = P.seg[s];
   const int64_t C = P.cols;
-  const int64_t r0 = 1 + ((int64_t)blockIdx.y - S.rb_begin) * RB;  // first own row (1-based)
+  const int64_t r0 = 1 + (rb - S.rb_begin) * RB;                   // first own row (1-based)
   const int64_t r1 = min(r0 + RB, S.rows + 1);                      // one past the last
   const int lane = threadIdx.x & 31;
   const int64_t c = ((int64_t)blockIdx.x * TX + threadIdx.x) * VW;
   const bool act = c < C;
-  const bool top = s == 0, bot = s == P.nseg - 1;
+  // zero rows outside the grid, unless the outer ghost rows hold a neighbour's rows
+  const bool top = s == 0 && !P.ext_top, bot = s == P.nseg - 1 && !P.ext_bot;
   const float wc = P.wc, wn = P.wn;
 
   float gwc = 0.f, gwn = 0.f;  // weight-gradient partials (WGRAD)
@@ -202,9 +204,10 @@ __global__ void k_halo(const __grid_constant__ HaloParams P) {
 
 }  // namespace
 
-cudaError_t launch_stencil(const StencilParams& p, cudaStream_t s) {
+cudaError_t launch_stencil(const StencilParams& p, int64_t nrb_launch, cudaStream_t s) {
+  if (nrb_launch <= 0) return cudaSuccess;
   const int vw = p.vec_ok ? 4 : 1;
-  dim3 grid((unsigned)((p.cols + (int64_t)TX * vw - 1) / ((int64_t)TX * vw)), (unsigned)p.nrb);
+  dim3 grid((unsigned)((p.cols + (int64_t)TX * vw - 1) / ((int64_t)TX * vw)), (unsigned)nrb_launch);
   if (p.acc) {
     if (p.vec_ok) k_stencil5<4, true><<<grid, TX, 0, s>>>(p);
     else k_stencil5<1, true><<<grid, TX, 0, s>>>(p);

@@ -396,8 +396,32 @@ def test_stencil_validation(lib):
     alias = md2(1 << 36)                                            # same storage as a
     assert S(a, alias, t, 1, 0.0, 0.25, None) == L.DR_E_INVAL
     assert lib.dr_stencil5_T(a, b, None, 3, 0.0, 0.25, None) == L.DR_E_INVAL
+    # one rank's share of a taller grid: one step per call, in and out agree on the flags
+    P = lib.dr_stencil5_part
+    assert P(a, b, 3, 0.0, 0.25, None) == L.DR_E_INVAL               # unknown row part
+    assert lib.dr_md2_set_external_halos(None, 1, 0) == L.DR_E_INVAL
+    assert lib.dr_md2_set_external_halos(a, 1, 1) == L.DR_OK
+    assert S(a, b, t, 2, 0.0, 0.25, None) == L.DR_E_INVAL            # exchange needed between steps
+    assert "one step per call" in L.last_error()
+    assert P(a, b, L.DR_ROWS_INNER, 0.0, 0.25, None) == L.DR_E_INVAL  # out's flags differ
+    assert "external halos" in L.last_error()
     for h in (a, b, t, other, wide, alias):
         lib.dr_md2_destroy(h)
+
+
+def test_scan_with_carry_validation(lib):
+    _, x = make_vec([100, 28])
+    _, o = make_vec([128], ptrs=[1 << 41])
+    v = view_of(x)
+    F = lib.dr_scan_with_carry
+    assert F(v, o, L.DR_PLUS, 0, None, None) == L.DR_E_INVAL          # a carry is required
+    assert F(v, o, L.DR_PLUS, 0, ctypes.c_void_p((1 << 42) + 2), None) == L.DR_E_ALIGN
+    assert F(v, o, L.DR_MUL, 0, ctypes.c_void_p(1 << 42), None) == L.DR_E_INVAL
+    _, o64 = make_vec([128], dtype=L.DR_F64, ptrs=[1 << 43])
+    assert F(v, o64, L.DR_PLUS, 1, ctypes.c_void_p(1 << 42), None) == L.DR_E_DTYPE
+    _, e = make_vec([0])
+    _, eo = make_vec([0], ptrs=[1 << 44])
+    assert F(view_of(e), eo, L.DR_PLUS, 1, ctypes.c_void_p(1 << 42), None) == L.DR_OK   # empty: no launch
 
 
 def test_scale_by_partner_validation(lib):
