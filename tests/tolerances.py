@@ -67,23 +67,48 @@ def stencil_f64_bound(steps: int, max_abs_u0: float) -> float:
 
 
 def black_scholes_bound(S, X, T, r, sigma, aux, u=U32):
-    """First-order bound on |price - price*| for Black-Scholes evaluated in a
-    precision with unit roundoff u (fp32: 2^-24) from the same inputs, against
-    the FP64 values.  The kernel's quantities each carry a few roundings and
-    one library call (log <= 1 ulp, exp <= 2 ulp, erfc <= 4 ulp for fp32; sqrt
-    and division correctly rounded), so 8u bounds each one's relative error:
-      d1:   E1 = 8u (1 + |ln(S/X)| + (r + sigma^2/2) T) / (sigma sqrt T) + 8u |d1|
-      d2:   E2 = E1 + 8u sigma sqrt T
-      N:    8u absolute (N = 1 - e or e with e = erfc(.)/2 <= 1/2)
-      K = X e^{-rT}:  8u (1 + rT) K
-    and a price S N(+-d1) -+ K N(+-d2) moves by at most the density times the
-    argument's error plus N's own error, per term, plus the final 2 roundings.
+    """First-order bound on |price - price*| for the library's Black-Scholes
+    element function evaluated with unit roundoff u on the same inputs, against
+    the FP64 prices.  Derived for the fp32 kernel's arithmetic (fp64, u = 2^-53,
+    calls log / exp / sqrt / erfc, which are within these budgets too):
+
+      q = S / X          __fdividef: 2 ulp                      -> rel 4u
+      lnr = log2(q) ln2  __log2f: abs 2^-22.6 on [0.5, 2], else 2 ulp; the
+                         multiply by ln2 (constant rounded):
+                         |err| <= A = ln2 2^-22.6 + 4u + 6u |ln q|
+      num = fma(drift, T, lnr)  drift = r + sigma^2/2 in two roundings
+                         (rel 2u); the fma rounds once: |err| <= A + 2u drift T + u |num|
+      m = (1/sigma) rsqrtf(T)   division 1u, rsqrtf 2 ulp (4u), product 1u -> rel 6u
+      d1 = num m         E1 = (A + 2u drift T) / (sigma sqrt T) + 8u |d1|
+      sv = sigma T rsqrtf(T)    rel 6u;  d2 = d1 - sv:  E2 = E1 + 6u sv + u |d2|
+      K = X __expf(-rT)  __expf: (2 + floor(1.173 rT)) ulp, rT rounded, product
+                         -> E_K = u (5 + 3.4 rT) K
+      N(-x), x = |d|     Zelen-Severo (Abramowitz & Stegun 26.2.17): absolute
+                         7.5e-8 in exact arithmetic; its fp32 evaluation
+                         (t = __fdividef(1, fma(p, x, 1)), phi via __expf with
+                         (2 + 1.173 x^2/2) ulp, four Horner fmas, rounded
+                         coefficients) is within rel (64 + 3 x^2) u of its
+                         value e <= min(1/2, phi(x) / x); N(x) = 1 - e adds u:
+                         E_N = 7.5e-8 + u + (64 + 3 x^2) u min(1/2, phi(x) / x)
+      C = S N(d1) - K N(d2), P = K N(-d2) - S N(-d1): each price moves by at most
+      S (phi(d1) E1 + E_N(d1)) + K (phi(d2) E2 + E_N(d2)) + E_K, plus the two
+      products and the subtraction: 2u (S + K).
     aux is the oracle's (phi(d1), phi(d2), d1, K) per option."""
     import numpy as np
     S, X, T = (np.asarray(v, np.float64) for v in (S, X, T))
     phi1, phi2, d1, K = aux[:, 0], aux[:, 1], aux[:, 2], aux[:, 3]
-    s = sigma * np.sqrt(T)
-    e1 = 8 * u * (1 + np.abs(np.log(S / X)) + (r + 0.5 * sigma * sigma) * T) / s + 8 * u * np.abs(d1)
-    e2 = e1 + 8 * u * s
-    eK = 8 * u * (1 + r * T) * K
-    return S * (phi1 * e1 + 8 * u) + K * (phi2 * e2 + 8 * u) + eK + 4 * u * (S + K)
+    sq = np.sqrt(T)
+    sv = sigma * sq
+    d2 = d1 - sv
+    drift = r + 0.5 * sigma * sigma
+    A = math.log(2.0) * 2.0 ** -22.6 + 4 * u + 6 * u * np.abs(np.log(S / X))
+    e1 = (A + 2 * u * drift * T) / sv + 8 * u * np.abs(d1)
+    e2 = e1 + 6 * u * sv + u * np.abs(d2)
+    eK = u * (5 + 3.4 * r * T) * K
+
+    def e_n(d, phi):
+        x = np.abs(d)
+        tail = np.minimum(0.5, np.where(x > 0, phi / np.maximum(x, 1e-300), 0.5))
+        return 7.5e-8 + u + (64 + 3 * x * x) * u * tail
+
+    return S * (phi1 * e1 + e_n(d1, phi1)) + K * (phi2 * e2 + e_n(d2, phi2)) + eK + 2 * u * (S + K)
