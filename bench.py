@@ -388,11 +388,14 @@ def measure_rows(api, dev, s, peak) -> dict:
     ms_batch = _time(lambda: batch.run_graph(stream=s), s, 20)
     ms_plain = _time(lambda: batch.run(stream=s), s, 20)
     ms_per = _time(lambda: batch.run_per_range(stream=s), s, 3)
+    ms_per_graph = _time(lambda: batch.run_per_range_graph(stream=s), s, 5)
     api.sync_status(s)
     rows["batched_4096_vectors"] = _row(
         ms_batch, 12 * tot, peak, elements=tot, tune=list(chosen), default_tune=list(default_tune),
         ms_default_tune=ms_default, ms_one_launch_no_graph=ms_plain, ms_one_launch_per_range=ms_per,
-        speedup_vs_per_range=ms_per / ms_batch, launches=1, per_range_launches=2 * len(shapes))
+        ms_one_launch_per_range_graph=ms_per_graph,
+        speedup_vs_per_range=ms_per / ms_batch, speedup_vs_per_range_graph=ms_per_graph / ms_batch,
+        launches=1, per_range_launches=2 * len(shapes))
     return rows
 
 

@@ -450,6 +450,12 @@ int dr_batch_run_graph(dr_batch* b, dr_stream_t stream);
  * transform_reduce-kernel launch per vector (2*nvec launches). */
 int dr_batch_run_per_range(dr_batch* b, dr_stream_t stream);
 
+/* The same 2*nvec launches captured once into a CUDA graph (on a private
+ * stream; the first call captures, later calls replay on `stream`): the
+ * per-range baseline without the host's per-launch cost, which separates the
+ * persistent launch's gain from saved launch overhead. */
+int dr_batch_run_per_range_graph(dr_batch* b, dr_stream_t stream);
+
 /* Autotuner: times every candidate launch shape on the plan `calib` (its
  * inputs must be initialized; its outputs are overwritten), picks the fastest
  * and stores it in the JSON cache at cache_path (NULL = $DR_TUNE_CACHE, else

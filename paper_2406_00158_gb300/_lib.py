@@ -11,7 +11,8 @@ import os
 import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdr_gb300.so")
+# DR_GB300_LIB selects another build of this library (e.g. the range-checked one)
+LIB_PATH = os.environ.get("DR_GB300_LIB") or os.path.join(_HERE, "libdr_gb300.so")
 
 # enum dr_status
 DR_OK, DR_E_INVAL, DR_E_DTYPE, DR_E_ALIGN, DR_E_CUDA, DR_E_TIMEOUT, DR_E_BOUNDS, DR_E_NOMEM, \
@@ -107,6 +108,7 @@ PROTOTYPES = {
     "dr_batch_run": (_I, [_P, _P]),
     "dr_batch_run_graph": (_I, [_P, _P]),
     "dr_batch_run_per_range": (_I, [_P, _P]),
+    "dr_batch_run_per_range_graph": (_I, [_P, _P]),
     "dr_batch_autotune": (_I, [_P, _I, ctypes.c_char_p, ctypes.POINTER(dr_tune)]),
 }
 

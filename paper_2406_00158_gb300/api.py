@@ -438,6 +438,10 @@ class Batch:
     def run_per_range(self, stream=None) -> None:
         call("dr_batch_run_per_range", self.handle, stream_handle(stream))
 
+    def run_per_range_graph(self, stream=None) -> None:
+        """The per-range baseline's launches captured once in a CUDA graph, replayed."""
+        call("dr_batch_run_per_range_graph", self.handle, stream_handle(stream))
+
     @property
     def tune(self) -> tuple:
         """(threads, items, ctas_per_sm, variant) of the batched kernel."""

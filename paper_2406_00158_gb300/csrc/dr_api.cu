@@ -649,6 +649,7 @@ extern "C" int dr_view_destroy(dr_view* v) {
     v->ws_scan.release();
     v->ws_reduce.release();
     v->ws_sort.release();
+    v->ws_table.release();
   }
   delete v;
   return DR_OK;
@@ -684,19 +685,36 @@ extern "C" int dr_view_segments(const dr_view* v, int max_pieces, dr_piece* out)
 // algorithms
 // ---------------------------------------------------------------------------
 
+// A table of more pieces than a launch carries inline goes to the view's device
+// table, uploaded on `s` (a stream-ordered copy from pageable memory: the call
+// waits for the stream's earlier work, and cannot be captured in a graph).
+template <typename P>
+static int place_pieces(dr_view* v, const std::vector<P>& pcs, P* inline_pc, const P** ext, cudaStream_t s) {
+  if (pcs.size() <= (size_t)kMaxPieces) {
+    std::copy(pcs.begin(), pcs.end(), inline_pc);
+    *ext = nullptr;
+    return DR_OK;
+  }
+  const size_t bytes = pcs.size() * sizeof(P);
+  if (int r = v->ws_table.ensure(bytes, s, 0)) return r;
+  cudaError_t e = cudaMemcpyAsync(v->ws_table.ptr, pcs.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "piece table upload");
+  v->ws_table.mark(s);
+  *ext = static_cast<const P*>(v->ws_table.ptr);
+  return DR_OK;
+}
+
 // The pieces of a call: the view's leaves (and the output, if any) re-segmented
 // together, each cut into tiles of `tile` elements.
-static int call_pieces(const dr_view* in, const dr_vec* out, int tile, KPiece* pc, int* npieces,
-                       int64_t* ntiles) {
+static std::vector<KPiece> build_pieces(const dr_view* in, const dr_vec* out, int tile, int64_t* ntiles) {
   std::vector<std::vector<Seg>> ops;
   for (int l = 0; l < in->nleaf; ++l) ops.push_back(in->leaf[l].vec->window(in->leaf[l].lo, in->leaf[l].hi));
   if (out) ops.push_back(out->window(0, in->size));
   const std::vector<Piece> ps = resegment(ops, esize(in->dtype));
-  if ((int)ps.size() > kMaxPieces)
-    return fail(DR_E_UNSUPPORTED, "call spans %zu segments after re-segmentation (limit %d)", ps.size(), kMaxPieces);
+  std::vector<KPiece> v(ps.size());
   int64_t t = 0;
   for (size_t i = 0; i < ps.size(); ++i) {
-    KPiece& k = pc[i];
+    KPiece& k = v[i];
     k.a = ps[i].p[0];
     k.b = in->nleaf == 2 ? ps[i].p[1] : nullptr;
     k.o = out ? ps[i].p[in->nleaf] : nullptr;
@@ -705,9 +723,23 @@ static int call_pieces(const dr_view* in, const dr_vec* out, int tile, KPiece* p
     k.vec_ok = ((uintptr_t)k.a % 16 == 0) && ((uintptr_t)k.b % 16 == 0) && ((uintptr_t)k.o % 16 == 0);
     t += (ps[i].len + tile - 1) / tile;
   }
-  *npieces = (int)ps.size();
   *ntiles = t;
-  return DR_OK;
+  return v;
+}
+
+// build_pieces, then up to kMaxPieces inline in `pc`; more go to the view's
+// device table (*ext), or are refused when ext == NULL.
+static int call_pieces(dr_view* in, const dr_vec* out, int tile, KPiece* pc, const KPiece** ext, int* npieces,
+                       int64_t* ntiles, cudaStream_t s) {
+  const std::vector<KPiece> v = build_pieces(in, out, tile, ntiles);
+  if (!ext && (int)v.size() > kMaxPieces)
+    return fail(DR_E_UNSUPPORTED, "call spans %zu segments after re-segmentation (limit %d)", v.size(), kMaxPieces);
+  *npieces = (int)v.size();
+  if (!ext) {
+    std::copy(v.begin(), v.end(), pc);
+    return DR_OK;
+  }
+  return place_pieces(in, v, pc, ext, s);
 }
 
 // True when [p, p + n) and [q, q + n) overlap but do not coincide.
@@ -741,7 +773,7 @@ static int do_scan(const char* who, const dr_view* in_c, dr_vec* out, int op, bo
   p.op = op;
   p.dtype = in->dtype;
   p.exclusive = exclusive ? 1 : 0;
-  if (int r = call_pieces(in, out, scan_tile_elems(in->dtype), p.pc, &p.npieces, &p.ntiles)) return r;
+  if (int r = call_pieces(in, out, scan_tile_elems(in->dtype), p.pc, &p.pc_ext, &p.npieces, &p.ntiles, s)) return r;
   if (int r = in->ws_scan.ensure(scan_ws_bytes(p.ntiles, in->dtype), s)) return r;
   p.ws = static_cast<char*>(in->ws_scan.ptr);
   p.status = status_word();
@@ -793,11 +825,14 @@ extern "C" int dr_transform_reduce(const dr_view* in_c, int op, const void* init
   p.dtype = in->dtype;
   p.result = dev_result;
   std::memcpy(&p.init_bits, init, esize(in->dtype));
-  if (int r = call_pieces(in, nullptr, reduce_tile_elems(in->dtype), p.pc, &p.npieces, &p.ntiles)) return r;
+  if (int r = call_pieces(in, nullptr, reduce_tile_elems(in->dtype), p.pc, &p.pc_ext, &p.npieces, &p.ntiles, s))
+    return r;
   const int grid = reduce_grid(in->dtype);
   if (int r = in->ws_reduce.ensure(reduce_ws_bytes(grid), s)) return r;
   p.ws = static_cast<char*>(in->ws_reduce.ptr);
+  p.ws_partials = grid;
   p.status = status_word();
+  if (!p.status) return fail(DR_E_CUDA, "%s: no device status word", who);
   cudaError_t e = launch_reduce(p, grid, s);
   in->ws_reduce.mark(s);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
@@ -877,9 +912,6 @@ extern "C" int dr_for_each(const dr_view* zip, int fn, const double* args, int n
   if (nargs < sig.nargs || (sig.nargs > 0 && !args))
     return fail(DR_E_INVAL, "%s: function %d needs %d scalar arguments", who, fn, sig.nargs);
   const int esz = esize(zip->dtype);
-  if ((int)zip->pieces.size() > kMaxPieces)
-    return fail(DR_E_UNSUPPORTED, "%s: %zu pieces after re-segmentation (limit %d)", who, zip->pieces.size(),
-                kMaxPieces);
   static thread_local ForEachParams p;
   std::memset(&p, 0, sizeof p);
   p.fn = fn;
@@ -887,7 +919,8 @@ extern "C" int dr_for_each(const dr_view* zip, int fn, const double* args, int n
   for (int a = 0; a < sig.nargs; ++a) p.arg[a] = args[a];
   const int tile = foreach_tile_elems(zip->dtype);
   int64_t t = 0;
-  int np = 0;
+  std::vector<FePiece> tab;
+  tab.reserve(zip->pieces.size());
   for (const Piece& q : zip->pieces) {
     if (q.len == 0) continue;
     for (int w = 0; w < sig.arity; ++w) {
@@ -896,7 +929,8 @@ extern "C" int dr_for_each(const dr_view* zip, int fn, const double* args, int n
         if (l != w && partial_overlap(q.p[w], q.p[l], q.len * esz))
           return fail(DR_E_INVAL, "%s: written operand %d overlaps operand %d", who, w, l);
     }
-    FePiece& k = p.pc[np++];
+    tab.emplace_back();
+    FePiece& k = tab.back();
     bool al = true;
     for (int l = 0; l < sig.arity; ++l) {
       k.p[l] = q.p[l];
@@ -907,9 +941,12 @@ extern "C" int dr_for_each(const dr_view* zip, int fn, const double* args, int n
     k.vec_ok = al;
     t += (q.len + tile - 1) / tile;
   }
-  p.npieces = np;
+  p.npieces = (int)tab.size();
   p.ntiles = t;
   if (t == 0) return DR_OK;
+  p.status = status_word();
+  if (!p.status) return fail(DR_E_CUDA, "%s: no device status word", who);
+  if (int r = place_pieces(const_cast<dr_view*>(zip), tab, p.pc, &p.pc_ext, (cudaStream_t)stream)) return r;
   cudaError_t e = launch_for_each(p, (cudaStream_t)stream);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
 }
@@ -927,13 +964,16 @@ extern "C" int dr_transform(const dr_view* in, dr_vec* out, dr_stream_t stream) 
   std::memset(&p, 0, sizeof p);
   p.vc = in->code();
   p.dtype = in->dtype;
-  if (int r = call_pieces(in, out, foreach_tile_elems(in->dtype), p.pc, &p.npieces, &p.ntiles)) return r;
+  const std::vector<KPiece> tab = build_pieces(in, out, foreach_tile_elems(in->dtype), &p.ntiles);
   const int esz = esize(in->dtype);
-  for (int i = 0; i < p.npieces; ++i) {
-    const KPiece& k = p.pc[i];
+  for (const KPiece& k : tab) {
     if (partial_overlap(k.o, k.a, k.len * esz) || (k.b && partial_overlap(k.o, k.b, k.len * esz)))
       return fail(DR_E_INVAL, "%s: output overlaps an operand of the view", who);
   }
+  p.npieces = (int)tab.size();
+  p.status = status_word();
+  if (!p.status) return fail(DR_E_CUDA, "%s: no device status word", who);
+  if (int r = place_pieces(const_cast<dr_view*>(in), tab, p.pc, &p.pc_ext, (cudaStream_t)stream)) return r;
   cudaError_t e = launch_transform(p, (cudaStream_t)stream);
   return e == cudaSuccess ? DR_OK : cuda_fail(e, who);
 }
@@ -957,7 +997,7 @@ extern "C" int dr_sort(const dr_view* in_c, dr_vec* out, dr_stream_t stream) {
   p.dtype = in->dtype;
   p.n = n;
   SortLaunch L{};
-  if (int r = call_pieces(in, nullptr, sort_tile_elems(in->dtype), p.in, &p.npin, &L.ntiles0)) return r;
+  if (int r = call_pieces(in, nullptr, sort_tile_elems(in->dtype), p.in, nullptr, &p.npin, &L.ntiles0, s)) return r;
   const std::vector<Seg> os = out->window(0, n);
   if ((int)os.size() > kMaxPieces) return fail(DR_E_UNSUPPORTED, "%s: output has more than %d segments", who, kMaxPieces);
   int64_t g = 0;
@@ -1026,9 +1066,12 @@ static int do_stencil(const char* who, dr_md2* in, dr_md2* out, dr_md2* tmp, int
     if (m)
       for (char* q : m->ptr) vec = vec && (uintptr_t)q % 16 == 0;
   const dr_md2* src = in;
+  unsigned* status = status_word();
+  if (!status) return fail(DR_E_CUDA, "%s: no device status word", who);
   for (int t = 0; t < steps; ++t) {
     dr_md2* dst = ((steps - 1 - t) % 2 == 0) ? out : tmp;
     std::memset(&p, 0, sizeof p);
+    p.status = status;
     p.nseg = nseg;
     p.cols = in->cols;
     p.nrb = nrb;

@@ -2,6 +2,7 @@
 // vectors), the one-launch run, its CUDA-graph replay, the one-launch-per-range
 // baseline, and the autotuner with its JSON cache.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -28,12 +29,12 @@ struct dr_batch {
   int device = -1;
   int64_t ntiles = 0;
   int64_t max_scan_tiles = 0;
-  BPiece* d_pieces = nullptr;
-  BTile* d_tiles = nullptr;
-  BVec* d_vecs = nullptr;
+  BDesc* d_desc = nullptr;  // one descriptor per tile of the current launch shape
   Workspace ws, ws_scan, ws_red;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t pr_graph = nullptr;      // the per-range baseline, captured
+  cudaGraphExec_t pr_gexec = nullptr;
   cudaStream_t cap = nullptr;
 
   void drop_graph() {
@@ -42,11 +43,15 @@ struct dr_batch {
     gexec = nullptr;
     graph = nullptr;
   }
+  void drop_pr_graph() {
+    if (pr_gexec) cudaGraphExecDestroy(pr_gexec);
+    if (pr_graph) cudaGraphDestroy(pr_graph);
+    pr_gexec = nullptr;
+    pr_graph = nullptr;
+  }
   void free_tables() {
-    if (d_tiles) cudaFree(d_tiles);
-    if (d_vecs) cudaFree(d_vecs);
-    d_tiles = nullptr;
-    d_vecs = nullptr;
+    if (d_desc) cudaFree(d_desc);
+    d_desc = nullptr;
   }
 };
 
@@ -60,24 +65,32 @@ static int upload(void** dst, const void* src, size_t bytes) {
   return e == cudaSuccess ? DR_OK : cuda_fail(e, "batch table upload");
 }
 
-// (Re)builds the tile table for the current launch shape and sizes the workspace.
+// (Re)builds the tile descriptors for the current launch shape and sizes the
+// workspace: every piece of every vector cut into tiles of threads * items
+// elements, vector after vector; an empty vector still gets one (empty) tile.
 static int build_tiles(dr_batch* b) {
   const int64_t TILE = (int64_t)b->tune.threads * b->tune.items;
-  std::vector<BTile> tiles;
-  std::vector<BVec> vecs(b->nvec);
+  std::vector<BDesc> desc;
   for (int v = 0; v < b->nvec; ++v) {
-    vecs[v].first_tile = (int64_t)tiles.size();
+    const int64_t first = (int64_t)desc.size();
     for (int k = b->vec_piece_begin[v]; k < b->vec_piece_begin[v + 1]; ++k) {
-      const int64_t len = b->pieces[k].len;
-      if (len == 0) tiles.push_back(BTile{k, 0, 0});  // an empty vector still gets one tile
-      for (int64_t off = 0; off < len; off += TILE) tiles.push_back(BTile{k, 0, off});
+      const BPiece& q = b->pieces[k];
+      if (q.len == 0) desc.push_back(BDesc{q.x, q.p, q.y, 0, 0, v, 0, 0});
+      for (int64_t off = 0; off < q.len; off += TILE) {
+        const int32_t len = (int32_t)std::min<int64_t>(TILE, q.len - off);
+        desc.push_back(BDesc{q.x + off, q.p + off, q.y + off, 0, len, v, 0, q.vec_ok && len == TILE ? 1 : 0});
+      }
     }
-    vecs[v].ntiles = (int32_t)((int64_t)tiles.size() - vecs[v].first_tile);
+    const int64_t nt = (int64_t)desc.size() - first;
+    if (nt > INT32_MAX) return fail(DR_E_UNSUPPORTED, "dr_batch_plan: vector %d has too many tiles", v);
+    for (int64_t i = first; i < (int64_t)desc.size(); ++i) {
+      desc[i].first_tile = first;
+      desc[i].ntiles = (int32_t)nt;
+    }
   }
   b->free_tables();
-  if (int r = upload((void**)&b->d_tiles, tiles.data(), tiles.size() * sizeof(BTile))) return r;
-  if (int r = upload((void**)&b->d_vecs, vecs.data(), vecs.size() * sizeof(BVec))) return r;
-  b->ntiles = (int64_t)tiles.size();
+  if (int r = upload((void**)&b->d_desc, desc.data(), desc.size() * sizeof(BDesc))) return r;
+  b->ntiles = (int64_t)desc.size();
   if (int r = b->ws.ensure(batch_ws_bytes(b->ntiles, b->nvec), nullptr)) return r;
   cudaError_t e = cudaDeviceSynchronize();
   return e == cudaSuccess ? DR_OK : cuda_fail(e, "batch plan");
@@ -136,8 +149,7 @@ extern "C" int dr_batch_plan(int nvec, const dr_vec* const* x, const dr_vec* con
     b->vec_piece_begin.push_back((int)b->pieces.size());
     b->total += n;
   }
-  int r = upload((void**)&b->d_pieces, b->pieces.data(), b->pieces.size() * sizeof(BPiece));
-  if (!r) r = build_tiles(b);
+  const int r = build_tiles(b);
   if (r) {
     dr_batch_destroy(b);
     return r;
@@ -150,9 +162,9 @@ extern "C" int dr_batch_destroy(dr_batch* b) {
   clear_error();
   if (!b) return DR_OK;
   b->drop_graph();
+  b->drop_pr_graph();
   if (b->cap) cudaStreamDestroy(b->cap);
   b->free_tables();
-  if (b->d_pieces) cudaFree(b->d_pieces);
   b->ws.release();
   b->ws_scan.release();
   b->ws_red.release();
@@ -179,9 +191,7 @@ extern "C" int dr_batch_get_tune(const dr_batch* b, dr_tune* tune) {
 
 static BatchParams params_of(const dr_batch* b) {
   BatchParams p{};
-  p.pieces = b->d_pieces;
-  p.tiles = b->d_tiles;
-  p.vecs = b->d_vecs;
+  p.desc = b->d_desc;
   p.ntiles = b->ntiles;
   p.nvec = b->nvec;
   p.ws = static_cast<char*>(b->ws.ptr);
@@ -224,14 +234,53 @@ extern "C" int dr_batch_run_graph(dr_batch* b, dr_stream_t stream) {
   return e == cudaSuccess ? DR_OK : cuda_fail(e, "cudaGraphLaunch");
 }
 
+static int per_range_workspaces(dr_batch* b, cudaStream_t s) {
+  if (int r = b->ws_scan.ensure(scan_ws_bytes(std::max<int64_t>(1, b->max_scan_tiles), DR_F32), s)) return r;
+  return b->ws_red.ensure(reduce_ws_bytes(reduce_grid(DR_F32)), s);
+}
+
+static int per_range_launches(dr_batch* b, cudaStream_t s);
+
 // One single-range scan launch and one single-range dot launch per vector.
 extern "C" int dr_batch_run_per_range(dr_batch* b, dr_stream_t stream) {
   clear_error();
   if (!b) return fail(DR_E_INVAL, "dr_batch_run_per_range: NULL plan");
   cudaStream_t s = (cudaStream_t)stream;
+  if (int r = per_range_workspaces(b, s)) return r;
+  return per_range_launches(b, s);
+}
+
+// The same launches captured once into a CUDA graph (on a private stream, with
+// the workspaces allocated before the capture) and replayed.
+extern "C" int dr_batch_run_per_range_graph(dr_batch* b, dr_stream_t stream) {
+  clear_error();
+  if (!b) return fail(DR_E_INVAL, "dr_batch_run_per_range_graph: NULL plan");
+  cudaError_t e;
+  if (!b->pr_gexec) {
+    if (!b->cap && (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "capture stream");
+    if (int r = per_range_workspaces(b, b->cap)) return r;
+    if ((e = cudaStreamSynchronize(b->cap)) != cudaSuccess) return cuda_fail(e, "capture stream");
+    if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    const int lr = per_range_launches(b, b->cap);
+    e = cudaStreamEndCapture(b->cap, &b->pr_graph);
+    if (lr) {
+      b->drop_pr_graph();
+      return lr;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if ((e = cudaGraphInstantiate(&b->pr_gexec, b->pr_graph, 0)) != cudaSuccess) {
+      b->drop_pr_graph();
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  e = cudaGraphLaunch(b->pr_gexec, (cudaStream_t)stream);
+  return e == cudaSuccess ? DR_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+static int per_range_launches(dr_batch* b, cudaStream_t s) {
   const int rgrid = reduce_grid(DR_F32);
-  if (int r = b->ws_scan.ensure(scan_ws_bytes(std::max<int64_t>(1, b->max_scan_tiles), DR_F32), s)) return r;
-  if (int r = b->ws_red.ensure(reduce_ws_bytes(rgrid), s)) return r;
   unsigned* status = status_word();
   if (!status) return fail(DR_E_CUDA, "dr_batch_run_per_range: no device status word");
   static thread_local ScanParams sp;
@@ -280,6 +329,7 @@ extern "C" int dr_batch_run_per_range(dr_batch* b, dr_stream_t stream) {
     rp.npieces = np;
     rp.ntiles = tr;
     rp.ws = static_cast<char*>(b->ws_red.ptr);
+    rp.ws_partials = rgrid;
     rp.status = status;
     rp.result = b->dots + v;
     if (np > 0) {

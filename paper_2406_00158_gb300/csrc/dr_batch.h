@@ -10,7 +10,7 @@
 
 namespace dr {
 
-struct BPiece {  // one piece of one vector: x, p, y re-segmented together
+struct BPiece {  // host side: one piece of one vector (x, p, y re-segmented together)
   const float* x;
   const float* p;
   float* y;
@@ -19,25 +19,25 @@ struct BPiece {  // one piece of one vector: x, p, y re-segmented together
   int32_t vec_ok;
 };
 
-struct BTile {  // a tile covers [off, min(off + TILE, len)) of piece `piece`
-  int32_t piece;
-  int32_t pad_;
-  int64_t off;
+// One tile of one vector, flattened on the host so that a tile costs the kernel
+// one 48-byte load (three independent 16-byte loads), not a chain of lookups.
+struct alignas(16) BDesc {
+  const float* x;       // x, p, y at the tile's first element
+  const float* p;
+  float* y;
+  int64_t first_tile;   // the vector's first tile
+  int32_t len;          // elements in this tile (<= the tile size; 0 for an empty vector)
+  int32_t vec;          // vector index
+  int32_t ntiles;       // tiles of the vector
+  int32_t full;         // len == tile size and x, p, y 16-byte aligned
 };
-
-struct BVec {  // the vector's tiles are [first_tile, first_tile + ntiles)
-  int64_t first_tile;
-  int32_t ntiles;
-  int32_t pad_;
-};
+static_assert(sizeof(BDesc) == 48, "descriptor size");
 
 struct BatchParams {
-  const BPiece* pieces;
-  const BTile* tiles;
-  const BVec* vecs;
+  const BDesc* desc;    // one per tile, vector after vector
   int64_t ntiles;
   int nvec;
-  char* ws;  // WsHeader | lookback slots | per-tile dot partials | per-vector counters
+  char* ws;  // WsHeader | per-vector counters | lookback slots | per-tile dot partials
   float* dots;
   unsigned* status;
   int64_t spin_limit;

@@ -382,6 +382,30 @@ __device__ __forceinline__ void raise_status(unsigned* status, unsigned code, un
   if (atomicCAS(status, 0u, code) == 0u) atomicExch(status + 1, info);
 }
 
+// Range-checked builds (-DDR_CHECKED=1): every global address a kernel forms is
+// checked against the bounds of the piece (segment, row block, tile) it belongs
+// to -- and, for a 16-byte access, its alignment -- before the access.  A
+// violation records DR_E_BOUNDS with the check's id in the device status word
+// (read by dr_sync_status) and the access is skipped instead of faulting.
+// Release builds compile the checks away.  Ids: scan 1xx, reduce 2xx, stencil
+// 3xx, for_each / transform 4xx, sort 5xx, batched 6xx.
+#ifndef DR_CHECKED
+#define DR_CHECKED 0
+#endif
+__device__ __forceinline__ bool chk(bool ok, unsigned id, unsigned* status) {
+  if (DR_CHECKED && !ok) raise_status(status, DR_E_BOUNDS, id);
+  return !DR_CHECKED || ok;
+}
+// A 16-byte access of elements [e0, e0 + n) of a piece of `len` elements at p.
+__device__ __forceinline__ bool chk_vec(int64_t e0, int n, int64_t len, const void* p, unsigned id,
+                                        unsigned* status) {
+  return chk(e0 >= 0 && e0 + n <= len && ((uintptr_t)p & 15) == 0, id, status);
+}
+// An access of element e of a piece of `len` elements.
+__device__ __forceinline__ bool chk_at(int64_t e, int64_t len, unsigned id, unsigned* status) {
+  return chk(e >= 0 && e < len, id, status);
+}
+
 // Polls slot i until it is valid for this epoch.  Bounded: gives up after
 // `limit` polls (or as soon as another wait on the device has given up),
 // records DR_E_TIMEOUT and returns P with the identity so the caller finishes.
@@ -499,15 +523,16 @@ __device__ __forceinline__ T warp_inclusive(T v, int lane) {
 // Warp-wide decoupled lookback.  Returns the combination of the published
 // values of tiles (pred, pred-1, ...) down to and including the nearest one in
 // the inclusive-prefix state; tiles before `lo` count as an inclusive prefix
-// equal to the identity.  Each round polls G slots per lane (32*G tiles, nearest
-// first: lane l holds pred - l*G - g), waits only for unpublished slots nearer
-// than the nearest inclusive prefix, and moves on by 32*G if there is none.
-// One round costs one L2 round trip; covering 32*G tiles per round keeps the
-// walk short even when hundreds of tiles are in flight.
+// equal to the identity.  Each round polls gr <= G slots per lane (32*gr tiles,
+// nearest first: lane l holds pred - l*gr - g), waits only for unpublished slots
+// nearer than the nearest inclusive prefix, and moves on by 32*gr if there is
+// none.  One round costs one L2 round trip; covering 32*gr tiles per round keeps
+// the walk short when hundreds of tiles are in flight at once.
 // --------------------------------------------------------------------------
 template <typename T, typename OPT, int G, typename S>
 __device__ __forceinline__ T lookback(const S& slots, int64_t pred, int64_t lo, unsigned tag, int lane,
-                                      int64_t limit, unsigned* status) {
+                                      int64_t limit, unsigned* status, int gr = G) {
+  // gr (1 <= gr <= G, uniform across the warp): slots polled per lane per round
   const T ident = OPT::template identity<T>();
   T run = ident;
   while (true) {
@@ -515,22 +540,22 @@ __device__ __forceinline__ T lookback(const S& slots, int64_t pred, int64_t lo, 
     unsigned st[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      const int64_t i = pred - (int64_t)(lane * G + g);
+      const int64_t i = pred - (int64_t)(lane * gr + g);
       val[g] = ident;
       st[g] = kStateP;
-      if (i >= lo) st[g] = slots.poll(i, tag, val[g]);
+      if (g < gr && i >= lo) st[g] = slots.poll(i, tag, val[g]);
     }
     int gp = G;  // this lane's nearest inclusive prefix
 #pragma unroll
     for (int g = G - 1; g >= 0; --g)
-      if (st[g] == kStateP) gp = g;
+      if (g < gr && st[g] == kStateP) gp = g;
     unsigned pm = __ballot_sync(0xffffffffu, gp < G);
     int fl = pm ? __ffs(pm) - 1 : 32;
     if (lane <= fl) {
 #pragma unroll
       for (int g = 0; g < G; ++g)
-        if (st[g] == 0 && (lane < fl || g < gp)) {
-          const int64_t i = pred - (int64_t)(lane * G + g);
+        if (g < gr && st[g] == 0 && (lane < fl || g < gp)) {
+          const int64_t i = pred - (int64_t)(lane * gr + g);
           st[g] = wait_slot<T, S, OPT>(slots, i, tag, val[g], limit, status);
         }
     }
@@ -538,16 +563,16 @@ __device__ __forceinline__ T lookback(const S& slots, int64_t pred, int64_t lo, 
     gp = G;
 #pragma unroll
     for (int g = G - 1; g >= 0; --g)
-      if (st[g] == kStateP) gp = g;
+      if (g < gr && st[g] == kStateP) gp = g;
     pm = __ballot_sync(0xffffffffu, gp < G);
     fl = pm ? __ffs(pm) - 1 : 32;
     T c = ident;
 #pragma unroll
     for (int g = 0; g < G; ++g)
-      if (lane < fl || (lane == fl && g <= gp)) c = OPT::apply(c, val[g]);
+      if (g < gr && (lane < fl || (lane == fl && g <= gp))) c = OPT::apply(c, val[g]);
     run = OPT::apply(warp_reduce<T, OPT::kOp>(c), run);
     if (pm) break;
-    pred -= 32 * G;
+    pred -= 32 * gr;
   }
   return run;
 }

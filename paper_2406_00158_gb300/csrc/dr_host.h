@@ -112,6 +112,7 @@ struct dr_view {
   int64_t size = 0;
   std::vector<dr::Piece> pieces;  // re-segmentation of the leaves' windows
   dr::Workspace ws_scan, ws_reduce, ws_sort;
+  dr::Workspace ws_table;  // piece table of calls with more pieces than fit in a launch
 
   void recompute();
   dr::KViewCode code() const;

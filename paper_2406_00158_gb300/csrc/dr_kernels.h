@@ -13,7 +13,11 @@
 namespace dr {
 
 constexpr int kMaxChain = 4;     // unary ops per chain in a fused view
-constexpr int kMaxPieces = 128;  // segments (after re-segmentation) per single-range call
+// Pieces (segments after re-segmentation) carried inline in a launch's
+// parameters; a scan, reduce, transform or for_each call with more pieces keeps
+// its whole piece table in device memory instead (pc_ext), the other calls
+// reject it.
+constexpr int kMaxPieces = 128;
 constexpr int kMaxZip = DR_MAX_ZIP;  // operands of a k-ary zip (and of one re-segmentation)
 
 // Fused view: element = post(zipop(pre0(a), pre1(b))) (or post(pre0(a)) for one leaf).
@@ -66,9 +70,11 @@ struct ReduceParams {
   int npieces;
   int64_t ntiles;
   char* ws;          // WsHeader + one partial (8 bytes) per CTA
+  int ws_partials;   // partial slots in ws (checked builds verify the grid fits)
   unsigned* status;  // per-device status word
   void* result;      // one element of dtype
   unsigned long long init_bits;
+  const KPiece* pc_ext;  // the piece table in device memory when npieces > kMaxPieces, else NULL
   KPiece pc[kMaxPieces];
 };
 
@@ -85,6 +91,7 @@ struct ScanParams {
   int64_t skip_tile;  // test hook: this logical tile never publishes (-1: none)
   unsigned long long init_bits;
   const void* carry;  // device carry-in (one element) or NULL; forward scans only
+  const KPiece* pc_ext;  // the piece table in device memory when npieces > kMaxPieces, else NULL
   KPiece pc[kMaxPieces];
 };
 
@@ -115,20 +122,24 @@ struct FePiece {
 };
 
 struct ForEachParams {
+  unsigned* status;  // per-device status word (checked builds)
   int fn;      // enum dr_foreach_fn
   int dtype;   // DR_F32 or DR_F64
   int npieces;
   int64_t ntiles;
   double arg[2];
+  const FePiece* pc_ext;  // the piece table in device memory when npieces > kMaxPieces, else NULL
   FePiece pc[kMaxPieces];
 };
 
 // transform: out = the fused view, piece by piece (KPiece a, b = leaves, o = out).
 struct TransformParams {
+  unsigned* status;  // per-device status word (checked builds)
   KViewCode vc;
   int dtype;
   int npieces;
   int64_t ntiles;
+  const KPiece* pc_ext;  // the piece table in device memory when npieces > kMaxPieces, else NULL
   KPiece pc[kMaxPieces];
 };
 
@@ -176,6 +187,7 @@ struct StencilSeg {
 };
 
 struct StencilParams {
+  unsigned* status;  // per-device status word (checked builds)
   int nseg;
   int64_t cols;
   int64_t nrb;       // total row blocks

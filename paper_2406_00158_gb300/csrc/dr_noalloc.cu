@@ -102,6 +102,7 @@ extern "C" int dr_dot_f32_noalloc(int nseg, const int64_t* lens, const float* co
   p.npieces = np;
   p.ntiles = tiles;
   p.ws = static_cast<char*>(scratch);
+  p.ws_partials = kNoAllocMaxCtas;
   p.status = status;
 
   cudaStream_t s = (cudaStream_t)stream;

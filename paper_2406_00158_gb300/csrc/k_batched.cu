@@ -5,9 +5,10 @@
 // thousands of short vectors that is launch-bound (cf. the launch fan-out cost
 // of a single-process runtime, Sec. 5 "Reduce").  Here every vector is cut into
 // tiles (per segment, as in the single-range kernels) and all tiles form one
-// global order, vector after vector.  Persistent CTAs take tiles from an
-// atomic ticket; each tile reads x and p once (128-bit), writes y once:
-// 12 B / element for both algorithms together.
+// global order, vector after vector, each described by one flat descriptor
+// (pointers at the tile, its length, the vector's first tile and tile count).
+// Persistent CTAs take tiles from an atomic ticket; each tile reads x and p once
+// (128-bit), writes y once: 12 B / element for both algorithms together.
 //  * scan carry: decoupled lookback over the tile's predecessors *within its
 //    vector* (the vector's first tile publishes its inclusive prefix directly);
 //  * dot: each tile writes its partial; the vector's last tile to finish
@@ -22,12 +23,66 @@ namespace {
 
 __device__ __forceinline__ float fadd(float a, float b) { return a + b; }
 
+// One tile descriptor: three independent 16-byte loads.
+__device__ __forceinline__ BDesc load_desc(const BDesc* d) {
+  const uint4* s = reinterpret_cast<const uint4*>(d);
+  const uint4 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2);
+  BDesc r;
+  memcpy(reinterpret_cast<char*>(&r), &a, 16);
+  memcpy(reinterpret_cast<char*>(&r) + 16, &b, 16);
+  memcpy(reinterpret_cast<char*>(&r) + 32, &c, 16);
+  return r;
+}
+
+// Workspace layout: header | per-vector counters | lookback slots | per-tile dot
+// partials (counters first: their offset does not depend on the tile count).
+struct BatchWs {
+  WsHeader* hdr;
+  unsigned* vcount;
+  Slots<float> slots;
+  float* dotpart;
+  __device__ BatchWs(const BatchParams& P) {
+    hdr = reinterpret_cast<WsHeader*>(P.ws);
+    vcount = reinterpret_cast<unsigned*>(P.ws + sizeof(WsHeader));
+    char* slot_base = P.ws + sizeof(WsHeader) + ((size_t)P.nvec * 4 + 15) / 16 * 16;
+    slots.bind(slot_base, P.ntiles);
+    dotpart = reinterpret_cast<float*>(slot_base + Slots<float>::bytes(P.ntiles));
+  }
+};
+
+// The vector's last tile to finish folds the dot partials in tile order (one
+// warp); `last` must be uniform across the warp.
+__device__ __forceinline__ void fold_dot(const BatchParams& P, const BatchWs& W, int vec, int64_t first,
+                                         int ntiles, int lane) {
+  __threadfence();
+  float acc = 0.f;
+  for (int64_t i = first + lane; i < first + ntiles; i += 32)
+    acc += __int_as_float((int)ld_relaxed_u32(reinterpret_cast<const unsigned*>(W.dotpart + i)));
+  acc = warp_reduce<float, DR_PLUS>(acc);
+  if (lane == 0) {
+    P.dots[vec] = acc;
+    W.vcount[vec] = 0;
+  }
+}
+
+__device__ __forceinline__ void finish_launch(const BatchWs& W) {
+  __threadfence();
+  if (atomicAdd(&W.hdr->done, 1u) == gridDim.x - 1) {
+    W.hdr->ticket = 0;
+    W.hdr->done = 0;
+    W.hdr->epoch = W.hdr->epoch + 1;
+    __threadfence();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Variant 0: one tile per CTA and iteration, held in registers.
+// ---------------------------------------------------------------------------
 template <int THREADS, int CH>
 __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ BatchParams P) {
   constexpr int NW = THREADS / 32;
   constexpr int Q = CH * NW;             // warp-chunk totals per tile
   constexpr int R = (Q + 31) / 32;       // entries per lane in warp 0
-  constexpr int TILE = THREADS * CH * 4;
   using O = Op<DR_PLUS>;
   __shared__ float s_tot[R * 32];
   __shared__ float s_off[R * 32];
@@ -35,34 +90,27 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
   __shared__ long long s_ticket;
   __shared__ int s_last;
 
-  WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
-  // layout: header | per-vector counters | lookback slots | per-tile dot partials
-  // (counters first: their offset does not depend on the tile count)
-  unsigned* vcount = reinterpret_cast<unsigned*>(P.ws + sizeof(WsHeader));
-  char* slot_base = P.ws + sizeof(WsHeader) + ((size_t)P.nvec * 4 + 15) / 16 * 16;
-  Slots<float> slots;
-  slots.bind(slot_base, P.ntiles);
-  float* dotpart = reinterpret_cast<float*>(slot_base + Slots<float>::bytes(P.ntiles));
-  const unsigned tag = (ld_relaxed_u32(&hdr->epoch) & 0x3fffffffu) << 2;
+  BatchWs W(P);
+  const unsigned tag = (ld_relaxed_u32(&W.hdr->epoch) & 0x3fffffffu) << 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   while (true) {
-    if (tid == 0) s_ticket = (long long)atomicAdd(&hdr->ticket, 1ull);
+    if (tid == 0) s_ticket = (long long)atomicAdd(&W.hdr->ticket, 1ull);
     __syncthreads();
     const int64_t t = s_ticket;
     if (t >= P.ntiles) break;
-    const BTile bt = P.tiles[t];
-    const BPiece pc = P.pieces[bt.piece];
-    const BVec bv = P.vecs[pc.vec];
-    const int64_t base = bt.off;
-    const bool full = pc.vec_ok && pc.len - base >= TILE;
+    const BDesc d = load_desc(P.desc + t);
 
     float x[CH][4], pr[CH][4];
-    if (full) {
+    if (d.full) {
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
-        V16<float> a = ld16<float>(pc.x + base + (int64_t)(c * THREADS + tid) * 4);
-        V16<float> b = ld16<float>(pc.p + base + (int64_t)(c * THREADS + tid) * 4);
+        const int e0 = (c * THREADS + tid) * 4;
+        V16<float> a, b;
+        if (chk_vec(e0, 4, d.len, d.x + e0, 600, P.status) && chk_vec(e0, 4, d.len, d.p + e0, 601, P.status)) {
+          a = ld16<float>(d.x + e0);
+          b = ld16<float>(d.p + e0);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           x[c][e] = a.v[e];
@@ -74,10 +122,10 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
       for (int c = 0; c < CH; ++c)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int64_t i = base + (int64_t)(c * THREADS + tid) * 4 + e;
-          const bool in = i < pc.len;
-          x[c][e] = in ? __ldg(pc.x + i) : 0.f;
-          pr[c][e] = in ? __ldg(pc.p + i) : 0.f;
+          const int i = (c * THREADS + tid) * 4 + e;
+          const bool in = i < d.len;
+          x[c][e] = in ? __ldg(d.x + i) : 0.f;
+          pr[c][e] = in ? __ldg(d.p + i) : 0.f;
         }
     }
 
@@ -119,7 +167,7 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
         float dt = 0.f;
 #pragma unroll
         for (int w = 0; w < NW; ++w) dt += s_dot[w];
-        dotpart[t] = dt;
+        W.dotpart[t] = dt;
       }
       // block-level scan of the Q warp-chunk totals: R consecutive entries per lane
       float loc[R];
@@ -136,14 +184,13 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
       if (lane == 0) exc = 0.f;
 
       float prefix = 0.f;
-      const int64_t first = bv.first_tile;
-      if (t == first) {
-        if (lane == 0) slots.publish(t, tag, kStateP, agg);
+      if (t == d.first_tile) {
+        if (lane == 0) W.slots.publish(t, tag, kStateP, agg);
       } else {
-        if (lane == 0) slots.publish(t, tag, kStateA, agg);
-        const float run = lookback<float, O, 4>(slots, t - 1, first, tag, lane, P.spin_limit, P.status);
+        if (lane == 0) W.slots.publish(t, tag, kStateA, agg);
+        const float run = lookback<float, O, 4>(W.slots, t - 1, d.first_tile, tag, lane, P.spin_limit, P.status);
         prefix = run;
-        if (lane == 0) slots.publish(t, tag, kStateP, prefix + agg);
+        if (lane == 0) W.slots.publish(t, tag, kStateP, prefix + agg);
       }
       float o = fadd(prefix, exc);
 #pragma unroll
@@ -161,66 +208,51 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
       float y[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) y[e] = fadd(pre, x[c][e]);
-      const int64_t off = base + (int64_t)(c * THREADS + tid) * 4;
-      if (full) {
+      const int off = (c * THREADS + tid) * 4;
+      if (d.full) {
         V16<float> q;
 #pragma unroll
         for (int e = 0; e < 4; ++e) q.v[e] = y[e];
-        st16<float>(pc.y + off, q);
+        if (chk_vec(off, 4, d.len, d.y + off, 602, P.status)) st16<float>(d.y + off, q);
       } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          if (off + e < pc.len) pc.y[off + e] = y[e];
+          if (off + e < d.len) d.y[off + e] = y[e];
       }
     }
 
     // the vector's last tile to finish combines the dot partials in tile order
     if (tid == 0) {
       __threadfence();
-      s_last = atomicAdd(vcount + pc.vec, 1u) == (unsigned)bv.ntiles - 1;
+      s_last = atomicAdd(W.vcount + d.vec, 1u) == (unsigned)d.ntiles - 1;
     }
     __syncthreads();
-    if (s_last && warp == 0) {
-      __threadfence();
-      float acc = 0.f;
-      for (int64_t i = bv.first_tile + lane; i < bv.first_tile + bv.ntiles; i += 32)
-        acc += __int_as_float((int)ld_relaxed_u32(reinterpret_cast<const unsigned*>(dotpart + i)));
-      acc = warp_reduce<float, DR_PLUS>(acc);
-      if (lane == 0) {
-        P.dots[pc.vec] = acc;
-        vcount[pc.vec] = 0;
-      }
-    }
+    if (s_last && warp == 0) fold_dot(P, W, d.vec, d.first_tile, d.ntiles, lane);
     __syncthreads();
   }
-
-  if (tid == 0) {
-    __threadfence();
-    if (atomicAdd(&hdr->done, 1u) == gridDim.x - 1) {
-      hdr->ticket = 0;
-      hdr->done = 0;
-      hdr->epoch = hdr->epoch + 1;
-      __threadfence();
-    }
-  }
+  if (tid == 0) finish_launch(W);
 }
 
 // ---------------------------------------------------------------------------
 // Variant 1: the lookahead pipeline of the single-range scan, per vector.
 // Iteration k of a persistent CTA:
 //   R phase, tile t_k: x and p arrive in a shared-memory stage by two TMA bulk
-//     copies issued an iteration earlier (full tiles; ragged ones load
-//     directly); the tile's dot partial is written and, if it is the last tile
-//     of its vector to finish, the vector's dot is folded; the scan tree of x
-//     runs and the tile aggregate is published (the vector's first tile
-//     publishes its inclusive prefix).
+//     copies issued two iterations earlier (full tiles; ragged ones load
+//     directly), with the tile's descriptor beside them; the dot partial and the
+//     scan tree of x run, and the tile aggregate is published (the vector's
+//     first tile publishes its inclusive prefix).
 //   S phase, tile t_{k-1}: warp 0 looks back within the vector, publishes the
 //     inclusive prefix, and the CTA re-reads x (an L2 hit), scans it with the
 //     carry and stores y.
+// Roles off warp 0's path (the lookback): warp 1 lane 0 takes tickets, loads
+// their descriptors and issues the bulk copies; warp 2 writes the dot partial
+// and, for the vector's last tile to finish, folds the vector's dot.
 // 12 B / element: x and p read once from HBM, y written once.
 // ---------------------------------------------------------------------------
 constexpr int LT = 256;  // threads per CTA
 constexpr int LNW = LT / 32;
+constexpr int kProducer = 32;  // warp 1, lane 0
+constexpr int kDotWarp = 2;
 
 template <int CH>
 struct LaGeom {
@@ -235,29 +267,26 @@ struct LaGeom {
 struct LaTile {  // what the S phase needs of the previous tile
   const float* x;
   float* y;
-  int64_t off, len, first;
+  int64_t first;
+  int len;
   bool full;
 };
 
+// Producer: loads tile t's descriptor into the stage's slot and starts the bulk
+// copies of x and p (full tiles), or completes the stage's barrier phase without
+// a copy.  One arrival per call either way, so the phase counts the stage's uses.
 template <int CH>
-__device__ __forceinline__ LaTile la_tile(const BatchParams& P, long long t) {
-  const BTile bt = P.tiles[t];
-  const BPiece pc = P.pieces[bt.piece];
-  const BVec bv = P.vecs[pc.vec];
-  return LaTile{pc.x, pc.y, bt.off, pc.len, bv.first_tile,
-                pc.vec_ok != 0 && pc.len - bt.off >= LaGeom<CH>::TILE};
-}
-
-template <int CH>
-__device__ __forceinline__ void la_issue(const BatchParams& P, long long t, char* stage, unsigned long long* bar) {
+__device__ __forceinline__ void la_fill(const BatchParams& P, long long t, char* stage, unsigned long long* bar,
+                                        BDesc* slot) {
   using G = LaGeom<CH>;
   if (t < P.ntiles) {
-    const BTile bt = P.tiles[t];
-    const BPiece pc = P.pieces[bt.piece];
-    if (pc.vec_ok && pc.len - bt.off >= G::TILE) {
+    const BDesc d = load_desc(P.desc + t);
+    *slot = d;
+    if (d.full && chk(d.len == G::TILE && ((uintptr_t)d.x & 15) == 0 && ((uintptr_t)d.p & 15) == 0, 605,
+                      P.status)) {
       mbar_expect_tx(bar, G::STAGE);
-      bulk_g2s(stage, pc.x + bt.off, G::XB, bar);
-      bulk_g2s(stage + G::XB, pc.p + bt.off, G::XB, bar);
+      bulk_g2s(stage, d.x, G::XB, bar);
+      bulk_g2s(stage + G::XB, d.p, G::XB, bar);
       return;
     }
   }
@@ -309,18 +338,13 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
   using O = Op<DR_PLUS>;
   extern __shared__ __align__(128) char s_stage[];  // 2 stages x (x tile | p tile)
   __shared__ __align__(8) unsigned long long s_bar[2];
+  __shared__ __align__(16) BDesc s_desc[2];         // descriptor of the tile in stage d
   __shared__ float s_totR[G::SR * 32], s_totS[G::SR * 32], s_off[G::SR * 32], s_dot[LNW];
-  __shared__ long long s_tk[3];
+  __shared__ long long s_tk[4];  // [0], [1]: first tickets; [2 + stage]: the ticket an iteration takes
   __shared__ float s_agg;
-  __shared__ int s_last;
 
-  WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
-  unsigned* vcount = reinterpret_cast<unsigned*>(P.ws + sizeof(WsHeader));
-  char* slot_base = P.ws + sizeof(WsHeader) + ((size_t)P.nvec * 4 + 15) / 16 * 16;
-  Slots<float> slots;
-  slots.bind(slot_base, P.ntiles);
-  float* dotpart = reinterpret_cast<float*>(slot_base + Slots<float>::bytes(P.ntiles));
-  const unsigned tag = (ld_relaxed_u32(&hdr->epoch) & 0x3fffffffu) << 2;
+  BatchWs W(P);
+  const unsigned tag = (ld_relaxed_u32(&W.hdr->epoch) & 0x3fffffffu) << 2;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned long long drop = l2_policy_evict_first();
 
@@ -328,9 +352,12 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
     mbar_init(&s_bar[0], 1);
     mbar_init(&s_bar[1], 1);
     fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == kProducer) {
     for (int d = 0; d < 2; ++d) {
-      s_tk[d] = (long long)atomicAdd(&hdr->ticket, 1ull);
-      la_issue<CH>(P, s_tk[d], s_stage + d * G::STAGE, &s_bar[d]);
+      s_tk[d] = (long long)atomicAdd(&W.hdr->ticket, 1ull);
+      la_fill<CH>(P, s_tk[d], s_stage + d * G::STAGE, &s_bar[d], &s_desc[d]);
     }
   }
   __syncthreads();
@@ -338,23 +365,24 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
   unsigned parity = 0;
   int sidx = 0;
   float aggprev = 0.f;  // warp 0
-  LaTile prev{nullptr, nullptr, 0, 0, 0, false};
+  LaTile prev{nullptr, nullptr, 0, 0, false};
 
   while (tk0 < P.ntiles || tprev >= 0) {
     const long long t = tk0;
     const bool haveR = t < P.ntiles, haveS = tprev >= 0;
-    LaTile cur{nullptr, nullptr, 0, 0, 0, false};
+    // the producer takes the next ticket now (used after barrier A)
+    long long tnew = P.ntiles;
+    if (tid == kProducer && tk1 < P.ntiles) tnew = (long long)atomicAdd(&W.hdr->ticket, 1ull);
+    LaTile cur{nullptr, nullptr, 0, 0, false};
     int vec = 0, vtiles = 0;
 
     // ---- R phase: dot partial and scan aggregate of tile t
     bool copy_lost = false;  // this thread's wait for the stage's bulk copies expired
     if (haveR) {
-      const BTile bt = P.tiles[t];
-      const BPiece pc = P.pieces[bt.piece];
-      const BVec bv = P.vecs[pc.vec];
-      vec = pc.vec;
-      vtiles = bv.ntiles;
-      cur = LaTile{pc.x, pc.y, bt.off, pc.len, bv.first_tile, pc.vec_ok != 0 && pc.len - bt.off >= G::TILE};
+      const BDesc d = s_desc[sidx];
+      vec = d.vec;
+      vtiles = d.ntiles;
+      cur = LaTile{d.x, d.y, d.first_tile, d.len, d.full != 0};
       float x[CH][4], pr[CH][4];
       if (cur.full) {
         copy_lost = !mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, kCopyWaitPolls, P.status);
@@ -374,10 +402,10 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
         for (int c = 0; c < CH; ++c)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int64_t i = bt.off + (int64_t)(c * LT + tid) * 4 + e;
-            const bool in = i < pc.len;
-            x[c][e] = in ? __ldg(pc.x + i) : 0.f;
-            pr[c][e] = in ? __ldg(pc.p + i) : 0.f;
+            const int i = (c * LT + tid) * 4 + e;
+            const bool in = i < d.len;
+            x[c][e] = in ? __ldg(d.x + i) : 0.f;
+            pr[c][e] = in ? __ldg(d.p + i) : 0.f;
           }
       }
       float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
@@ -393,9 +421,7 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
       float wx[CH];
       la_local_scan<CH>(x, wx, s_totR, lane, warp);
     }
-    long long tnew = P.ntiles;
-    if (tid == 0 && tk1 < P.ntiles) tnew = (long long)atomicAdd(&hdr->ticket, 1ull);
-    if (__syncthreads_or(copy_lost)) {
+    if (__syncthreads_or(copy_lost)) {  // ---- barrier A: s_totR, s_dot; the R stage is read
       // A bulk copy did not complete within its bound (DR_E_TIMEOUT is recorded):
       // no stage is read or re-armed any more; wait, again bounded, for copies
       // that may still be in flight into either stage, then leave.
@@ -404,6 +430,15 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
       __syncthreads();
       break;
     }
+#ifndef DR_BATCH_LATE_REFILL
+#define DR_BATCH_LATE_REFILL 0
+#endif
+    if (!DR_BATCH_LATE_REFILL && tid == kProducer) {
+      // every read of the stage consumed in this R phase happened before barrier A
+      s_tk[2 + sidx] = tnew;
+      fence_proxy_async_smem();
+      la_fill<CH>(P, tnew, s_stage + sidx * G::STAGE, &s_bar[sidx], &s_desc[sidx]);
+    }
 
     float prefix = 0.f;
     if (warp == 0) {
@@ -411,33 +446,25 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
         float loc[G::SR], exc;
         const float agg = la_block_totals<CH>(s_totR, lane, loc, exc);
         if (lane == 0) {
-          slots.publish(t, tag, t == cur.first ? kStateP : kStateA, agg);
+          W.slots.publish(t, tag, t == cur.first ? kStateP : kStateA, agg);
           s_agg = agg;
-          float dt = 0.f;
-#pragma unroll
-          for (int w = 0; w < LNW; ++w) dt += s_dot[w];
-          dotpart[t] = dt;
-          __threadfence();
-          s_last = atomicAdd(vcount + vec, 1u) == (unsigned)vtiles - 1;
-        }
-        __syncwarp();
-        if (__shfl_sync(0xffffffffu, lane == 0 ? s_last : 0, 0)) {
-          // the vector's last tile to finish folds the dot partials in tile order
-          __threadfence();
-          float acc = 0.f;
-          for (int64_t i = cur.first + lane; i < cur.first + vtiles; i += 32)
-            acc += __int_as_float((int)ld_relaxed_u32(reinterpret_cast<const unsigned*>(dotpart + i)));
-          acc = warp_reduce<float, DR_PLUS>(acc);
-          if (lane == 0) {
-            P.dots[vec] = acc;
-            vcount[vec] = 0;
-          }
         }
       }
       if (haveS && tprev != prev.first) {
-        prefix = lookback<float, O, 1>(slots, tprev - 1, prev.first, tag, lane, P.spin_limit, P.status);
-        if (lane == 0) slots.publish(tprev, tag, kStateP, prefix + aggprev);
+        prefix = lookback<float, O, 1>(W.slots, tprev - 1, prev.first, tag, lane, P.spin_limit, P.status);
+        if (lane == 0) W.slots.publish(tprev, tag, kStateP, prefix + aggprev);
       }
+    } else if (warp == kDotWarp && haveR) {
+      int last = 0;
+      if (lane == 0) {
+        float dt = 0.f;
+#pragma unroll
+        for (int w = 0; w < LNW; ++w) dt += s_dot[w];
+        W.dotpart[t] = dt;
+        __threadfence();
+        last = atomicAdd(W.vcount + vec, 1u) == (unsigned)vtiles - 1;
+      }
+      if (__shfl_sync(0xffffffffu, last, 0)) fold_dot(P, W, vec, cur.first, vtiles, lane);
     }
 
     // ---- S phase: y of tile tprev
@@ -446,7 +473,9 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
       if (prev.full) {
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-          const V16<float> a = ld16_hint<float>(prev.x + prev.off + (int64_t)(c * LT + tid) * 4, drop);
+          const int e0 = (c * LT + tid) * 4;
+          V16<float> a;
+          if (chk_vec(e0, 4, prev.len, prev.x + e0, 604, P.status)) a = ld16_hint<float>(prev.x + e0, drop);
 #pragma unroll
           for (int e = 0; e < 4; ++e) x[c][e] = a.v[e];
         }
@@ -455,12 +484,12 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
         for (int c = 0; c < CH; ++c)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const int64_t i = prev.off + (int64_t)(c * LT + tid) * 4 + e;
+            const int i = (c * LT + tid) * 4 + e;
             x[c][e] = i < prev.len ? __ldg(prev.x + i) : 0.f;
           }
       }
       la_local_scan<CH>(x, wexc, s_totS, lane, warp);
-      __syncthreads();
+      __syncthreads();  // ---- barrier B: s_totS
       if (warp == 0) {
         float loc[G::SR], exc;
         la_block_totals<CH>(s_totS, lane, loc, exc);
@@ -472,49 +501,42 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
           o = fadd(o, loc[r]);
         }
       }
-      __syncthreads();
+      __syncthreads();  // ---- barrier C: s_off
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const float pre = fadd(s_off[c * LNW + warp], wexc[c]);
-        const int64_t off = prev.off + (int64_t)(c * LT + tid) * 4;
+        const int off = (c * LT + tid) * 4;
         if (prev.full) {
           V16<float> q;
 #pragma unroll
           for (int e = 0; e < 4; ++e) q.v[e] = fadd(pre, x[c][e]);
-          st16_hint<float>(prev.y + off, q, drop);
+          if (chk_vec(off, 4, prev.len, prev.y + off, 603, P.status)) st16_hint<float>(prev.y + off, q, drop);
         } else {
 #pragma unroll
           for (int e = 0; e < 4; ++e)
             if (off + e < prev.len) prev.y[off + e] = fadd(pre, x[c][e]);
         }
       }
+    } else {
+      __syncthreads();  // the reads of s_totR and s_dot end before the next R phase rewrites them
     }
-    if (tid == 0) s_tk[2] = tnew;
-    __syncthreads();
-    const long long tn = tk1 < P.ntiles ? s_tk[2] : P.ntiles;
-    if (tid == 0) {
-      fence_proxy_async_smem();  // every read of stage sidx happened before the barriers above
-      la_issue<CH>(P, tn, s_stage + sidx * G::STAGE, &s_bar[sidx]);
+    if (DR_BATCH_LATE_REFILL) {
+      if (tid == kProducer) {
+        s_tk[2 + sidx] = tnew;
+        fence_proxy_async_smem();
+        la_fill<CH>(P, tnew, s_stage + sidx * G::STAGE, &s_bar[sidx], &s_desc[sidx]);
+      }
+      __syncthreads();
     }
     parity ^= 1u << sidx;
-    if (warp == 0) aggprev = s_agg;
+    if (warp == 0) aggprev = haveR ? s_agg : 0.f;
     prev = cur;
     tprev = haveR ? t : -1;
     tk0 = tk1;
-    tk1 = tn;
+    tk1 = s_tk[2 + sidx];  // written by the producer before barrier B (or the plain barrier)
     sidx ^= 1;
-    __syncthreads();
   }
-
-  if (tid == 0) {
-    __threadfence();
-    if (atomicAdd(&hdr->done, 1u) == gridDim.x - 1) {
-      hdr->ticket = 0;
-      hdr->done = 0;
-      hdr->epoch = hdr->epoch + 1;
-      __threadfence();
-    }
-  }
+  if (tid == 0) finish_launch(W);
 }
 
 template <int CH, int MINB>

@@ -179,15 +179,23 @@ struct Fn<float, DR_FE_BLACK_SCHOLES> {
   }
 };
 
-template <typename T, int FN>
-__device__ __forceinline__ int find_fe_piece(const ForEachParams& P, int64_t tile) {
-  int lo = 0, hi = P.npieces - 1;
+// The piece holding `tile`, from a table of n pieces sorted by first tile.
+template <typename PC>
+__device__ __forceinline__ int find_tile_piece(const PC* pc, int n, int64_t tile) {
+  int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (P.pc[mid].tile_begin <= tile) lo = mid;
+    if (pc[mid].tile_begin <= tile) lo = mid;
     else hi = mid - 1;
   }
   return lo;
+}
+
+// The inline table (kernel parameters) or the device table, searched in separate
+// branches so that each keeps its address space.
+template <typename T, int FN>
+__device__ __forceinline__ int find_fe_piece(const ForEachParams& P, int64_t tile) {
+  return P.pc_ext ? find_tile_piece(P.pc_ext, P.npieces, tile) : find_tile_piece(P.pc, P.npieces, tile);
 }
 
 template <typename T, int FN>
@@ -200,15 +208,20 @@ __global__ void __launch_bounds__(FT) k_for_each(const __grid_constant__ ForEach
   const unsigned long long pol = l2_policy_evict_first();
   const int tid = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
-    const FePiece& pc = P.pc[find_fe_piece<T, FN>(P, tile)];
+    const int k = find_fe_piece<T, FN>(P, tile);
+    const FePiece& pc = P.pc_ext ? P.pc_ext[k] : P.pc[k];
     const int64_t base = (tile - pc.tile_begin) * TILE;
+    if (!chk(k >= 0 && k < P.npieces && base >= 0 && base < pc.len, 400, P.status)) continue;
     if (pc.vec_ok && pc.len - base >= TILE) {
       V16<T> xv[FCH][F::NIN];
 #pragma unroll
       for (int c = 0; c < FCH; ++c) {
-        const int64_t off = (base + (int64_t)(c * FT + tid) * VN) * (int64_t)sizeof(T);
+        const int64_t e0 = base + (int64_t)(c * FT + tid) * VN;
+        const int64_t off = e0 * (int64_t)sizeof(T);
 #pragma unroll
-        for (int j = 0; j < F::NIN; ++j) xv[c][j] = ld16_stream<T>(pc.p[F::in(j)] + off, pol);
+        for (int j = 0; j < F::NIN; ++j)
+          if (chk_vec(e0, VN, pc.len, pc.p[F::in(j)] + off, 401, P.status))
+            xv[c][j] = ld16_stream<T>(pc.p[F::in(j)] + off, pol);
       }
 #pragma unroll
       for (int c = 0; c < FCH; ++c) {
@@ -224,11 +237,14 @@ __global__ void __launch_bounds__(FT) k_for_each(const __grid_constant__ ForEach
           for (int o = 0; o < F::NOUT; ++o) yv[o].v[e] = yo[o];
         }
 #pragma unroll
-        for (int o = 0; o < F::NOUT; ++o) st16_hint<T>(pc.p[F::out(o)] + off, yv[o], pol);
+        for (int o = 0; o < F::NOUT; ++o)
+          if (chk_vec(off / (int64_t)sizeof(T), VN, pc.len, pc.p[F::out(o)] + off, 402, P.status))
+            st16_hint<T>(pc.p[F::out(o)] + off, yv[o], pol);
       }
     } else {
       const int64_t end = min(base + (int64_t)TILE, pc.len);
       for (int64_t i = base + tid; i < end; i += FT) {
+        if (!chk_at(i, pc.len, 403, P.status)) continue;
         T xi[F::NIN], yo[F::NOUT];
 #pragma unroll
         for (int j = 0; j < F::NIN; ++j) xi[j] = reinterpret_cast<const T*>(pc.p[F::in(j)])[i];
@@ -244,13 +260,7 @@ __global__ void __launch_bounds__(FT) k_for_each(const __grid_constant__ ForEach
 // transform: out = view (KIND 0: one plain leaf; 1: a * b; 2: interpreted chain)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int find_tr_piece(const TransformParams& P, int64_t tile) {
-  int lo = 0, hi = P.npieces - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (P.pc[mid].tile_begin <= tile) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
+  return P.pc_ext ? find_tile_piece(P.pc_ext, P.npieces, tile) : find_tile_piece(P.pc, P.npieces, tile);
 }
 
 template <typename T, int KIND>
@@ -270,15 +280,18 @@ __global__ void __launch_bounds__(FT) k_transform(const __grid_constant__ Transf
   const unsigned long long pol = l2_policy_evict_first();
   const int tid = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
-    const KPiece& pc = P.pc[find_tr_piece(P, tile)];
+    const int k = find_tr_piece(P, tile);
+    const KPiece& pc = P.pc_ext ? P.pc_ext[k] : P.pc[k];
     const int64_t base = (tile - pc.tile_begin) * TILE;
+    if (!chk(k >= 0 && k < P.npieces && base >= 0 && base < pc.len, 410, P.status)) continue;
     if (pc.vec_ok && pc.len - base >= TILE) {
       V16<T> av[FCH], bv[FCH];
 #pragma unroll
       for (int c = 0; c < FCH; ++c) {
-        const int64_t off = (base + (int64_t)(c * FT + tid) * VN) * (int64_t)sizeof(T);
-        av[c] = ld16_stream<T>(pc.a + off, pol);
-        if (two) bv[c] = ld16_stream<T>(pc.b + off, pol);
+        const int64_t e0 = base + (int64_t)(c * FT + tid) * VN;
+        const int64_t off = e0 * (int64_t)sizeof(T);
+        if (chk_vec(e0, VN, pc.len, pc.a + off, 411, P.status)) av[c] = ld16_stream<T>(pc.a + off, pol);
+        if (two && chk_vec(e0, VN, pc.len, pc.b + off, 412, P.status)) bv[c] = ld16_stream<T>(pc.b + off, pol);
       }
       if constexpr (KIND == 2) {
         T xa[FCH][VN], xb[FCH][VN];
@@ -302,11 +315,12 @@ __global__ void __launch_bounds__(FT) k_transform(const __grid_constant__ Transf
 #pragma unroll
         for (int e = 0; e < VN; ++e)
           o.v[e] = KIND == 2 ? av[c].v[e] : tr_eval<T, KIND>(ve, av[c].v[e], two ? bv[c].v[e] : T(0));
-        st16_hint<T>(pc.o + off, o, pol);
+        if (chk_vec(off / (int64_t)sizeof(T), VN, pc.len, pc.o + off, 413, P.status)) st16_hint<T>(pc.o + off, o, pol);
       }
     } else {
       const int64_t end = min(base + (int64_t)TILE, pc.len);
       for (int64_t i = base + tid; i < end; i += FT) {
+        if (!chk_at(i, pc.len, 414, P.status)) continue;
         const T a = reinterpret_cast<const T*>(pc.a)[i];
         const T b = two ? reinterpret_cast<const T*>(pc.b)[i] : T(0);
         reinterpret_cast<T*>(pc.o)[i] = tr_eval<T, KIND>(ve, a, b);

@@ -76,17 +76,27 @@ __global__ void __launch_bounds__(RT, RCTAS) k_reduce(const __grid_constant__ Re
   for (int e = 0; e < V; ++e) acc[e] = O::template identity<T>();
 
   for (int64_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
-    const KPiece& pc = P.pc[find_piece(P.pc, P.npieces, tile)];
+    // the inline table (kernel parameters) or the device table, searched in
+    // separate branches so that each keeps its address space
+    const int k = P.pc_ext ? find_piece(P.pc_ext, P.npieces, tile) : find_piece(P.pc, P.npieces, tile);
+    const KPiece& pc = P.pc_ext ? P.pc_ext[k] : P.pc[k];
     const int64_t base = (tile - pc.tile_begin) * TILE;
+    if (!chk(k >= 0 && k < P.npieces && base >= 0 && base < pc.len, 200, P.status)) continue;
     if (pc.vec_ok && pc.len - base >= TILE) {
       V16<T> ra[RCH], rb[RCH];
 #pragma unroll
-      for (int c = 0; c < RCH; ++c)
-        ra[c] = ld16<T>(pc.a + (base + (int64_t)(c * RT + tid) * V) * (int64_t)sizeof(T));
+      for (int c = 0; c < RCH; ++c) {
+        const int64_t e0 = base + (int64_t)(c * RT + tid) * V;
+        const char* pa = pc.a + e0 * (int64_t)sizeof(T);
+        if (chk_vec(e0, V, pc.len, pa, 201, P.status)) ra[c] = ld16<T>(pa);
+      }
       if (two) {
 #pragma unroll
-        for (int c = 0; c < RCH; ++c)
-          rb[c] = ld16<T>(pc.b + (base + (int64_t)(c * RT + tid) * V) * (int64_t)sizeof(T));
+        for (int c = 0; c < RCH; ++c) {
+          const int64_t e0 = base + (int64_t)(c * RT + tid) * V;
+          const char* pb = pc.b + e0 * (int64_t)sizeof(T);
+          if (chk_vec(e0, V, pc.len, pb, 202, P.status)) rb[c] = ld16<T>(pb);
+        }
       }
       if constexpr (KIND == 2) {
         T xa[RCH][V], xb[RCH][V];
@@ -136,7 +146,7 @@ __global__ void __launch_bounds__(RT, RCTAS) k_reduce(const __grid_constant__ Re
   WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
   unsigned long long* part = reinterpret_cast<unsigned long long*>(P.ws + sizeof(WsHeader));
   if (tid == 0) {
-    part[blockIdx.x] = to_bits(v);
+    if (chk(blockIdx.x < (P.ws_partials ? P.ws_partials : gridDim.x), 203, P.status)) part[blockIdx.x] = to_bits(v);
     __threadfence();
     s_last = atomicAdd(&hdr->done, 1u) == gridDim.x - 1;
   }

@@ -75,16 +75,6 @@ __device__ __forceinline__ int find_piece(const KPiece* pc, int n, int64_t tile)
   return lo;
 }
 
-// DR_CHECKED builds range- and alignment-check every address of the kernel; a
-// violation records DR_E_BOUNDS (with the check's id) in the status word and
-// the access is skipped instead of faulting.
-#ifndef DR_CHECKED
-#define DR_CHECKED 0
-#endif
-__device__ __forceinline__ bool chk(bool ok, unsigned id, unsigned* status) {
-  if (DR_CHECKED && !ok) raise_status(status, DR_E_BOUNDS, id);
-  return !DR_CHECKED || ok;
-}
 
 // Where a logical tile lives.
 struct TileRef {
@@ -96,8 +86,17 @@ struct TileRef {
 template <typename T, bool REV>
 __device__ __forceinline__ TileRef tile_ref(const ScanParams& P, long long lt) {
   const int64_t pt = REV ? P.ntiles - 1 - lt : lt;
-  const int k = find_piece(P.pc, P.npieces, pt);
-  const KPiece* pc = &P.pc[k];
+  // search the inline table (kernel parameters: constant-cache loads) or the
+  // device table in separate branches, so that each keeps its address space
+  int k;
+  const KPiece* pc;
+  if (P.pc_ext) {
+    k = find_piece(P.pc_ext, P.npieces, pt);
+    pc = &P.pc_ext[k];
+  } else {
+    k = find_piece(P.pc, P.npieces, pt);
+    pc = &P.pc[k];
+  }
   const int64_t base = (pt - pc->tile_begin) * stile<T>();
   const bool ok = chk(lt >= 0 && lt < P.ntiles && k >= 0 && k < P.npieces && base >= 0 && base < pc->len, 100,
                       P.status);

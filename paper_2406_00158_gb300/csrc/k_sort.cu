@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const __grid_constant__ Sor
   for (int i = 0; i < SIT; ++i) {
     if (cnt == STILE || w * 32 * SIT + i * 32 + lane < cnt) {
       const int di = (int)((key[i] >> shift) & 255);
-      skeys[dstart[di] + whist[w][di] + rank[i]] = key[i];
+      const unsigned at = dstart[di] + whist[w][di] + rank[i];
+      if (chk(at < (unsigned)STILE, 500, P.status)) skeys[at] = key[i];
     }
   }
   __syncthreads();
@@ -351,7 +352,9 @@ __global__ void __launch_bounds__(ST) k_sort_scatter(const __grid_constant__ Sor
         if (ostart[mid] <= (int64_t)g) lo = mid;
         else hi = mid - 1;
       }
-      reinterpret_cast<T*>(P.out[lo].p)[(int64_t)g - ostart[lo]] = KO::from(k);
+      const int64_t seg_end = lo + 1 < P.npout ? ostart[lo + 1] : P.n;
+      if (chk((int64_t)g >= ostart[lo] && (int64_t)g < seg_end, 501, P.status))
+        reinterpret_cast<T*>(P.out[lo].p)[(int64_t)g - ostart[lo]] = KO::from(k);
     }
   }
 }

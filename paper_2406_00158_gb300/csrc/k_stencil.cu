@@ -51,11 +51,14 @@ struct Row {
   float w, e;  // west of v[0] (lane 0 only), east of v[VW-1] (lane 31 only)
 };
 
+// Row g (0 .. nrows-1, ghost rows included) of a block allocation of nrows x C.
 template <int VW>
 __device__ __forceinline__ void load_row(Row<VW>& r, const float* in, int64_t g, int64_t C, int64_t c,
-                                         bool zero_row, int lane) {
-  const bool act = c < C;
-  if (zero_row || !act) {
+                                         bool zero_row, int lane, int64_t nrows, unsigned* status) {
+  const bool load = !zero_row && c < C &&
+                    chk(g >= 0 && g < nrows && c + VW <= C && (VW == 1 || ((uintptr_t)(in + g * C + c) & 15) == 0),
+                        300, status);
+  if (!load) {
 #pragma unroll
     for (int e = 0; e < VW; ++e) r.v[e] = 0.f;
   } else if constexpr (VW == 4) {
@@ -67,7 +70,7 @@ __device__ __forceinline__ void load_row(Row<VW>& r, const float* in, int64_t g,
   }
   r.w = 0.f;
   r.e = 0.f;
-  if (!zero_row && act) {
+  if (load) {
     if (lane == 0 && c > 0) r.w = __ldg(in + g * C + c - 1);
     if (lane == 31 && c + VW < C) r.e = __ldg(in + g * C + c + VW);
   }
@@ -103,15 +106,17 @@ __global__ void __launch_bounds__(TX, DR_STENCIL_MINB) k_stencil5(const __grid_c
 
   float gwc = 0.f, gwn = 0.f;  // weight-gradient partials (WGRAD)
   Row<VW> up, cur;
-  load_row<VW>(up, S.in, r0 - 1, C, c, top && r0 - 1 == 0, lane);
-  load_row<VW>(cur, S.in, r0, C, c, false, lane);
+  const int64_t nrows = S.rows + 2;
+  if (!chk(s >= 0 && s < P.nseg && r0 >= 1 && r0 <= S.rows, 301, P.status)) return;
+  load_row<VW>(up, S.in, r0 - 1, C, c, top && r0 - 1 == 0, lane, nrows, P.status);
+  load_row<VW>(cur, S.in, r0, C, c, false, lane, nrows, P.status);
 
   for (int64_t r = r0; r < r1; r += G) {
     Row<VW> nx[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
       const int64_t g = r + 1 + k;
-      if (g <= r1) load_row<VW>(nx[k], S.in, g, C, c, bot && g == S.rows + 1, lane);
+      if (g <= r1) load_row<VW>(nx[k], S.in, g, C, c, bot && g == S.rows + 1, lane, nrows, P.status);
     }
 #pragma unroll
     for (int k = 0; k < G; ++k) {
@@ -125,7 +130,7 @@ __global__ void __launch_bounds__(TX, DR_STENCIL_MINB) k_stencil5(const __grid_c
         float o[VW];
         float pv[VW];
         if constexpr (WGRAD) {
-          if (act) {
+          if (act && chk(row >= 1 && row <= S.rows && c + VW <= C, 302, P.status)) {
             if constexpr (VW == 4) {
               const V16<float> q = ld16<float>(S.prev + row * C + c);
 #pragma unroll
@@ -149,7 +154,8 @@ __global__ void __launch_bounds__(TX, DR_STENCIL_MINB) k_stencil5(const __grid_c
             gwn = __fmaf_rn(nsum, pv[e], gwn);
           }
         }
-        if (act) {
+        if (act && chk(row >= 1 && row <= S.rows && c + VW <= C &&
+                           (VW == 1 || ((uintptr_t)(S.out + row * C + c) & 15) == 0), 303, P.status)) {
           float* dst = S.out + row * C + c;
           // a block's first / last own row also goes to the neighbours' ghost rows
           float* g_up = (row == 1 && S.out_prev) ? S.out_prev + (S.prev_rows + 1) * C + c : nullptr;

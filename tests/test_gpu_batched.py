@@ -74,6 +74,11 @@ def test_batch_small_vs_oracle_repeat_graph_per_range(api, tune):
     b.run_per_range()
     api.sync_status()
     check(x, p, shapes, ys, dots, tile=G.scan_tile(torch.float32))
+    for _ in range(2):          # captured once, replayed
+        dots.fill_(float("nan"))
+        b.run_per_range_graph()
+        api.sync_status()
+        check(x, p, shapes, ys, dots, tile=G.scan_tile(torch.float32))
 
 
 def test_batch_non_aligned_partner(api):
@@ -110,7 +115,7 @@ def test_batch_full_config_exact_integer_valued(api):
     dots = torch.full((len(shapes),), float("nan"), dtype=torch.float32, device="cuda")
     b = api.Batch(xs, ps, ys, dots)
     starts = np.concatenate([[0], np.cumsum([sum(sh) for sh in shapes])])
-    for run in (b.run_graph, b.run_per_range):
+    for run in (b.run_graph, b.run_per_range, b.run_per_range_graph):
         dots.fill_(float("nan"))
         run()
         api.sync_status()
