@@ -154,6 +154,15 @@ int dr_block_lengths(int64_t n, int p, int64_t* lens_out);
 int dr_vec_create(int dtype, int nseg, const int64_t* lens, void* const* seg_ptrs, dr_vec** out);
 int dr_vec_destroy(dr_vec* v);
 
+/* Points the vector's segments at new storage of the same lengths (seg_ptrs:
+ * one device pointer per segment, rules as for dr_vec_create).  Views built on
+ * the vector follow it -- their next call uses the new storage -- and keep the
+ * device workspaces they allocated, so a caller that runs an algorithm on a new
+ * set of equally shaped tensors every step (an autograd function, a training
+ * loop) allocates no workspace after the first step.  Launches already made
+ * keep the storage they were given.  Host only. */
+int dr_vec_rebind(dr_vec* v, void* const* seg_ptrs);
+
 /* Shape queries (host only). */
 int dr_vec_info(const dr_vec* v, int* dtype, int* nseg, int64_t* n);
 int dr_vec_segment(const dr_vec* v, int k, void** ptr, int64_t* len, int64_t* start);

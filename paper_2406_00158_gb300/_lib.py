@@ -67,6 +67,7 @@ PROTOTYPES = {
     "dr_block_lengths": (_I, [_I64, _I, _PI64]),
     "dr_vec_create": (_I, [_I, _I, _PI64, _PP, _PP]),
     "dr_vec_destroy": (_I, [_P]),
+    "dr_vec_rebind": (_I, [_P, _PP]),
     "dr_vec_info": (_I, [_P, _PI, _PI, _PI64]),
     "dr_vec_segment": (_I, [_P, _I, _PP, _PI64, _PI64]),
     "dr_vec_locate": (_I, [_P, _I64, _PI, _PI64]),

@@ -79,7 +79,8 @@ class SegmentedVector:
                 raise ValueError("segments must be 1-D contiguous tensors of one dtype")
         self.segments = segs
         self.dtype = dt
-        lens = (ctypes.c_int64 * len(segs))(*[s.numel() for s in segs])
+        self._lens = [s.numel() for s in segs]
+        lens = (ctypes.c_int64 * len(segs))(*self._lens)
         ptrs = _ptr_array([s.data_ptr() for s in segs])
         h = _handle_out()
         call("dr_vec_create", _DT[dt], len(segs), lens, ptrs, ctypes.byref(h))
@@ -99,6 +100,19 @@ class SegmentedVector:
             s.copy_(t[off:off + s.numel()])
             off += s.numel()
         return v
+
+    def rebind(self, segments: Sequence[torch.Tensor]) -> "SegmentedVector":
+        """Points this vector at new tensors of the same segment lengths and
+        dtype; its views follow and keep their device workspaces."""
+        segs = list(segments)
+        if len(segs) != len(self._lens):
+            raise ValueError("rebind needs one tensor per segment")
+        for s, n in zip(segs, self._lens):
+            if s.dtype != self.dtype or s.dim() != 1 or not s.is_contiguous() or s.numel() != n:
+                raise ValueError("rebind: segments must match in dtype, length and be 1-D contiguous")
+        call("dr_vec_rebind", self.handle, _ptr_array([s.data_ptr() for s in segs]))
+        self.segments = segs
+        return self
 
     @property
     def n(self) -> int:

@@ -14,6 +14,7 @@ pass is the library's kernels (the tensors are only plumbing).
 """
 from __future__ import annotations
 
+import threading
 from typing import Sequence
 
 import torch
@@ -25,23 +26,79 @@ def _contig(ts):
     return [t.contiguous() for t in ts]
 
 
+def _segments_like(lens, dtype, device):
+    """Output segments in one allocation, each starting on a 16-byte boundary
+    (so the kernels keep their 128-bit path)."""
+    esz = torch.empty((), dtype=dtype).element_size()
+    a = 16 // esz
+    offs, pos = [], 0
+    for n in lens:
+        offs.append(pos)
+        pos += (int(n) + a - 1) // a * a
+    buf = torch.empty(max(pos, 1), dtype=dtype, device=device)
+    return [buf[o:o + int(n)] for o, n in zip(offs, lens)]
+
+
+class _Plan:
+    """An input vector, its view and an output vector for one shape (segment
+    lengths, dtype, device), rebound to each call's tensors: the view's device
+    workspace is allocated on the first call only.  One per thread, so that
+    calls on different threads never share a workspace."""
+
+    def __init__(self, xs, ys):
+        self.x = api.SegmentedVector(xs)
+        self.view = self.x.view()
+        self.y = api.SegmentedVector(ys)
+
+    def bind(self, xs, ys):
+        self.x.rebind(xs)
+        self.y.rebind(ys)
+
+    def release(self):
+        # drop this call's tensors (launches already made keep their storage)
+        self.x.segments = []
+        self.y.segments = []
+
+
+_plans = threading.local()
+
+
+def _plan(kind, xs, ys):
+    cache = getattr(_plans, "d", None)
+    if cache is None:
+        cache = _plans.d = {}
+    key = (kind, tuple(t.numel() for t in xs), xs[0].dtype, xs[0].device)
+    p = cache.get(key)
+    if p is None:
+        if len(cache) >= 32:
+            cache.clear()
+        p = cache[key] = _Plan(xs, ys)
+    else:
+        p.bind(xs, ys)
+    return p
+
+
 class _ScanFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, *segs):
-        x = api.SegmentedVector(_contig(segs))
-        y = api.SegmentedVector.empty([s.numel() for s in segs], segs[0].dtype, segs[0].device)
-        api.inclusive_scan(x.view(), y)
-        ctx.lens = [s.numel() for s in segs]
-        return tuple(y.segments)
+        xs = _contig(segs)
+        lens = [s.numel() for s in xs]
+        ys = _segments_like(lens, xs[0].dtype, xs[0].device)
+        p = _plan("scan", xs, ys)
+        api.inclusive_scan(p.view, p.y)
+        p.release()
+        ctx.lens = lens
+        return tuple(ys)
 
     @staticmethod
     def backward(ctx, *gys):
         dev = next(g for g in gys if g is not None).device
         gys = [g.contiguous() if g is not None else torch.zeros(n, device=dev) for g, n in zip(gys, ctx.lens)]
-        g = api.SegmentedVector(gys)
-        gx = api.SegmentedVector.empty(ctx.lens, gys[0].dtype, dev)
-        api.reverse_inclusive_scan(g.view(), gx)
-        return tuple(gx.segments)
+        gxs = _segments_like(ctx.lens, gys[0].dtype, dev)
+        p = _plan("reverse_scan", gys, gxs)
+        api.reverse_inclusive_scan(p.view, p.y)
+        p.release()
+        return tuple(gxs)
 
 
 def inclusive_scan(segments: Sequence[torch.Tensor]) -> tuple:

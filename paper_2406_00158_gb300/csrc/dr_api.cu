@@ -357,6 +357,18 @@ extern "C" int dr_vec_create(int dtype, int nseg, const int64_t* lens, void* con
   return DR_OK;
 }
 
+extern "C" int dr_vec_rebind(dr_vec* v, void* const* seg_ptrs) {
+  clear_error();
+  if (!v || !seg_ptrs) return fail(DR_E_INVAL, "dr_vec_rebind: NULL argument");
+  for (size_t k = 0; k < v->ptr.size(); ++k) {
+    if (v->len[k] > 0 && !seg_ptrs[k]) return fail(DR_E_INVAL, "dr_vec_rebind: segment %zu pointer is NULL", k);
+    if ((uintptr_t)seg_ptrs[k] % v->esz)
+      return fail(DR_E_ALIGN, "dr_vec_rebind: segment %zu pointer not aligned to %d bytes", k, v->esz);
+  }
+  for (size_t k = 0; k < v->ptr.size(); ++k) v->ptr[k] = static_cast<char*>(seg_ptrs[k]);
+  return DR_OK;
+}
+
 extern "C" int dr_vec_destroy(dr_vec* v) {
   clear_error();
   delete v;
@@ -912,6 +924,7 @@ extern "C" int dr_for_each(const dr_view* zip, int fn, const double* args, int n
   if (nargs < sig.nargs || (sig.nargs > 0 && !args))
     return fail(DR_E_INVAL, "%s: function %d needs %d scalar arguments", who, fn, sig.nargs);
   const int esz = esize(zip->dtype);
+  const_cast<dr_view*>(zip)->recompute();  // its vectors may have been rebound to new storage
   static thread_local ForEachParams p;
   std::memset(&p, 0, sizeof p);
   p.fn = fn;

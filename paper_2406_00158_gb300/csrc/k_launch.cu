@@ -9,6 +9,10 @@ cudaError_t launch_scan_f32(const ScanParams& p, bool reverse, int grid, cudaStr
 cudaError_t launch_scan_f64(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
 cudaError_t launch_scan_i64(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
 cudaError_t launch_scan_i32(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
+cudaError_t launch_scan_f32_ext(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
+cudaError_t launch_scan_f64_ext(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
+cudaError_t launch_scan_i64_ext(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
+cudaError_t launch_scan_i32_ext(const ScanParams& p, bool reverse, int grid, cudaStream_t s);
 cudaError_t launch_reduce_f32(const ReduceParams& p, int grid, cudaStream_t s);
 cudaError_t launch_reduce_f64(const ReduceParams& p, int grid, cudaStream_t s);
 cudaError_t launch_reduce_i64(const ReduceParams& p, int grid, cudaStream_t s);
@@ -25,6 +29,14 @@ size_t scan_ws_bytes(int64_t ntiles, int dtype) {
 int scan_grid(int, int64_t) { return 0; }  // 0: occupancy-sized persistent grid
 
 cudaError_t launch_scan(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
+  if (p.pc_ext) {  // more pieces than the kernel parameters hold: the device-table kernels
+    switch (p.dtype) {
+      case DR_F32: return launch_scan_f32_ext(p, reverse, grid, s);
+      case DR_F64: return launch_scan_f64_ext(p, reverse, grid, s);
+      case DR_I64: return launch_scan_i64_ext(p, reverse, grid, s);
+      default: return launch_scan_i32_ext(p, reverse, grid, s);
+    }
+  }
   switch (p.dtype) {
     case DR_F32: return launch_scan_f32(p, reverse, grid, s);
     case DR_F64: return launch_scan_f64(p, reverse, grid, s);

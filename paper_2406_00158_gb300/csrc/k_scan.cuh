@@ -54,10 +54,19 @@ constexpr int SQ = SCH * SNW;     // warp-chunk totals per tile
 constexpr int SR = SQ / 32;       // totals per lane of warp 0
 constexpr int kLookbackG = DR_SCAN_LOOKBACK_G;  // lookback slots per lane per round
 constexpr int kMinBlocks = DR_SCAN_MINB;        // resident CTAs per SM
-constexpr int kStages = 2;        // shared-memory stages: the tile being reduced + the next
+constexpr int kStages = 2;        // tiles ticketed ahead: the tile being reduced + the next
 constexpr int kTileBytes = ST * SCH * 16;
 
-constexpr int smem_bytes() { return kStages * kTileBytes; }
+// A zip view (KIND 3) keeps the view's values of a reduced tile in its stage
+// until the tile's S phase, instead of re-reading both leaves from L2: one
+// more stage (the tile being reduced, the next one, and the one awaiting its S
+// phase), 96 KB per CTA at two CTAs per SM.
+template <int KIND>
+__host__ __device__ constexpr bool keeps_view() { return false && KIND == 3; }
+template <int KIND>
+__host__ __device__ constexpr int smem_stages() { return keeps_view<KIND>() ? kStages + 1 : kStages; }
+template <int KIND>
+__host__ __device__ constexpr int smem_bytes() { return smem_stages<KIND>() * kTileBytes; }
 static_assert(SQ % 32 == 0, "block-level scan assumes a multiple of 32 totals");
 
 template <typename T>
@@ -76,6 +85,16 @@ __device__ __forceinline__ int find_piece(const KPiece* pc, int n, int64_t tile)
 }
 
 
+// The piece table of a launch: inline in the kernel parameters (read through
+// the constant cache), or, with EXT, in device memory (a call of more than
+// kMaxPieces pieces).  A compile-time choice, so that each kernel knows the
+// address space of every piece access.
+template <bool EXT>
+__device__ __forceinline__ const KPiece* piece_table(const ScanParams& P) {
+  if constexpr (EXT) return P.pc_ext;
+  else return P.pc;
+}
+
 // Where a logical tile lives.
 struct TileRef {
   const KPiece* pc;
@@ -83,20 +102,12 @@ struct TileRef {
   bool full;     // a whole, 16-byte aligned tile: 128-bit path
 };
 
-template <typename T, bool REV>
+template <typename T, bool REV, bool EXT>
 __device__ __forceinline__ TileRef tile_ref(const ScanParams& P, long long lt) {
+  const KPiece* tab = piece_table<EXT>(P);
   const int64_t pt = REV ? P.ntiles - 1 - lt : lt;
-  // search the inline table (kernel parameters: constant-cache loads) or the
-  // device table in separate branches, so that each keeps its address space
-  int k;
-  const KPiece* pc;
-  if (P.pc_ext) {
-    k = find_piece(P.pc_ext, P.npieces, pt);
-    pc = &P.pc_ext[k];
-  } else {
-    k = find_piece(P.pc, P.npieces, pt);
-    pc = &P.pc[k];
-  }
+  const int k = find_piece(tab, P.npieces, pt);
+  const KPiece* pc = &tab[k];
   const int64_t base = (pt - pc->tile_begin) * stile<T>();
   const bool ok = chk(lt >= 0 && lt < P.ntiles && k >= 0 && k < P.npieces && base >= 0 && base < pc->len, 100,
                       P.status);
@@ -213,11 +224,11 @@ __device__ __forceinline__ T block_totals(const T* s_tot, int lane, T (&loc)[SR]
 // a stage's barrier phase counts its uses.
 // With two leaves (a zip view), the tile's range of leaf b is prefetched into
 // L2 at the same time, so the R phase's loads of b hit L2.
-template <typename T, bool REV>
+template <typename T, bool REV, bool EXT>
 __device__ __forceinline__ void stage_issue(const ScanParams& P, long long lt, char* stage,
                                             unsigned long long* bar, bool two = false) {
   if (lt < P.ntiles) {
-    const TileRef r = tile_ref<T, REV>(P, lt);
+    const TileRef r = tile_ref<T, REV, EXT>(P, lt);
     if (r.full) {
       mbar_expect_tx(bar, kTileBytes);
       bulk_g2s(stage, r.pc->a + r.base * (int64_t)sizeof(T), kTileBytes, bar);
@@ -233,12 +244,14 @@ __device__ __forceinline__ void stage_issue(const ScanParams& P, long long lt, c
 // registers, so the one-leaf view keeps the plain kernel's occupancy).
 // REV: scan from the last element to the first (reverse inclusive scan).
 // EXCL: exclusive scan with init.
-template <typename T, int OP, int KIND, bool REV, bool EXCL>
+template <typename T, int OP, int KIND, bool REV, bool EXCL, bool EXT>
 __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
   constexpr int V = 16 / sizeof(T);
+  constexpr bool KEEP = keeps_view<KIND>();
+  constexpr int NST = smem_stages<KIND>();
   using O = Op<OP>;
-  extern __shared__ __align__(128) char s_stage[];  // kStages x kTileBytes
-  __shared__ __align__(8) unsigned long long s_bar[kStages];
+  extern __shared__ __align__(128) char s_stage[];  // NST x kTileBytes
+  __shared__ __align__(8) unsigned long long s_bar[NST];
   __shared__ T s_totR[SQ], s_totS[SQ], s_off[SQ];
   __shared__ long long s_tk[kStages + 1];
   __shared__ T s_agg;
@@ -266,11 +279,11 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
 
   // prologue: tickets of the first kStages tiles (in order) and their loads
   if (tid == 0) {
-    for (int d = 0; d < kStages; ++d) mbar_init(&s_bar[d], 1);
+    for (int d = 0; d < NST; ++d) mbar_init(&s_bar[d], 1);
     fence_mbar_init();
     for (int d = 0; d < kStages; ++d) {
       s_tk[d] = (long long)atomicAdd(&hdr->ticket, 1ull);
-      stage_issue<T, REV>(P, s_tk[d], s_stage + d * kTileBytes, &s_bar[d], two);
+      stage_issue<T, REV, EXT>(P, s_tk[d], s_stage + d * kTileBytes, &s_bar[d], two);
     }
   }
   __syncthreads();
@@ -278,6 +291,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
 #pragma unroll
   for (int d = 0; d < kStages; ++d) tk[d] = s_tk[d];
   unsigned parity = 0;    // bit d: phase parity of stage d's next completion
+  unsigned pend = (1u << kStages) - 1;  // bit d: stage d has an issue not yet consumed
   long long tprev = -1;
   T aggprev = ident;  // warp 0: aggregate of tprev
   int sidx = 0;       // stage of tk[0]
@@ -289,7 +303,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     // ---- R phase: aggregate of tile t (from its stage; ragged tiles load directly)
     bool copy_lost = false;  // this thread's wait for the stage's bulk copy expired
     if (haveR) {
-      const TileRef rr = tile_ref<T, REV>(P, t);
+      const TileRef rr = tile_ref<T, REV, EXT>(P, t);
       T x[SCH][V], wx[SCH];
       if (rr.full) {
         copy_lost = !mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, kCopyWaitPolls, P.status);
@@ -298,7 +312,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
         for (int c = 0; c < SCH; ++c) {
           V16<T> va;
           const char* sp = st + (c * ST + tid) * 16;
-          if (chk(sidx >= 0 && sidx < kStages && ((uintptr_t)sp & 15) == 0, 103, P.status))
+          if (chk(sidx >= 0 && sidx < NST && ((uintptr_t)sp & 15) == 0, 103, P.status))
             va = *reinterpret_cast<const V16<T>*>(sp);
           V16<T> vb;
           if (two) vb = ld16_hint<T>(rr.pc->b + (rr.base + (int64_t)(c * ST + tid) * V) * (int64_t)sizeof(T), keep);
@@ -314,6 +328,18 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
         V16<T> na[SCH], nb[SCH];
         tile_values<T, KIND>(rr, two, tid, ve, ident, na, nb, x);
       }
+      if constexpr (KEEP) {
+        // the view's values stay in the stage (each thread its own chunks) for the
+        // tile's S phase in the next iteration
+        char* st = s_stage + sidx * kTileBytes;
+#pragma unroll
+        for (int c = 0; c < SCH; ++c) {
+          V16<T> v;
+#pragma unroll
+          for (int e = 0; e < V; ++e) v.v[e] = x[c][e];
+          *reinterpret_cast<V16<T>*>(st + (c * ST + tid) * 16) = v;
+        }
+      }
       local_scan<T, OP, REV>(x, wx, s_totR, lane, warp, ident);
     }
     // the ticket after the staged ones (needed only at the end of the iteration)
@@ -325,7 +351,8 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
       // no stage is read or re-armed any more; wait, again bounded, for the
       // copies that may still be in flight into either stage, then leave.
       if (tid == 0)
-        for (int d = 0; d < kStages; ++d) mbar_wait(&s_bar[d], (parity >> d) & 1u, kCopyWaitPolls, P.status);
+        for (int d = 0; d < NST; ++d)
+          if (pend >> d & 1u) mbar_wait(&s_bar[d], (parity >> d) & 1u, kCopyWaitPolls, P.status);
       __syncthreads();
       break;
     }
@@ -346,13 +373,25 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
       }
     }
 
-    // ---- S phase: re-read tile tprev (L2), scan it with its carry and store it
+    // ---- S phase: tile tprev again -- re-read from L2, or (a zip view) its view
+    // values from the stage the R phase left them in -- scanned with its carry, stored
     if (haveS) {
-      const TileRef rs = tile_ref<T, REV>(P, tprev);
-      V16<T> sa[SCH], sb[SCH];
-      if (rs.full) load_full<T>(rs, two, tid, drop, sa, sb, P.status);
+      const TileRef rs = tile_ref<T, REV, EXT>(P, tprev);
       T x[SCH][V], wexc[SCH];
-      tile_values<T, KIND>(rs, two, tid, ve, ident, sa, sb, x);
+      if constexpr (KEEP) {
+        const char* st = s_stage + ((sidx + NST - 1) % NST) * kTileBytes;
+#pragma unroll
+        for (int c = 0; c < SCH; ++c) {
+          const V16<T> v = *reinterpret_cast<const V16<T>*>(st + (c * ST + tid) * 16);
+#pragma unroll
+          for (int e = 0; e < V; ++e) x[c][e] = v.v[e];
+        }
+        fence_proxy_async_smem();  // generic writes above precede the stage's next bulk copy
+      } else {
+        V16<T> sa[SCH], sb[SCH];
+        if (rs.full) load_full<T>(rs, two, tid, drop, sa, sb, P.status);
+        tile_values<T, KIND>(rs, two, tid, ve, ident, sa, sb, x);
+      }
       local_scan<T, OP, REV>(x, wexc, s_totS, lane, warp, ident);
       __syncthreads();
       if (warp == 0) {
@@ -398,20 +437,24 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     }
     if (tid == 0) s_tk[kStages] = tnew;
     __syncthreads();  // s_tk, s_agg published; shared totals free
-    // refill the stage read in this R phase with the next ticketed tile (all reads
-    // of it happened before the barriers above)
+    // refill the stage whose tile is done -- the one read in this R phase, or for a
+    // zip view the one read in this S phase -- with the next ticketed tile (all
+    // reads of it happened before the barriers above); it is reduced two
+    // iterations from now
     const long long tn = tlast < P.ntiles ? s_tk[kStages] : P.ntiles;
+    const int fill = (sidx + kStages) % NST;
     if (tid == 0) {
       fence_proxy_async_smem();
-      stage_issue<T, REV>(P, tn, s_stage + sidx * kTileBytes, &s_bar[sidx], two);
+      stage_issue<T, REV, EXT>(P, tn, s_stage + fill * kTileBytes, &s_bar[fill], two);
     }
     parity ^= 1u << sidx;
+    pend = (pend & ~(1u << sidx)) | (1u << fill);
     if (warp == 0) aggprev = s_agg;
     tprev = haveR ? t : -1;
 #pragma unroll
     for (int d = 0; d < kStages - 1; ++d) tk[d] = tk[d + 1];
     tk[kStages - 1] = tn;
-    sidx = (sidx + 1) % kStages;
+    sidx = (sidx + 1) % NST;
     __syncthreads();
   }
 
@@ -429,39 +472,146 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
   }
 }
 
-template <typename T, int OP, int KIND, bool REV, bool EXCL>
+// ---------------------------------------------------------------------------
+// One wave: a plain forward scan whose tiles all fit in one wave of resident
+// CTAs (e.g. 2^20 int64 = 256 tiles).  Every tile is in flight at once, so the
+// lookahead pipeline above only adds latency (a bulk copy, a second ticket, a
+// re-read of the tile); here a CTA takes one ticket, keeps its tile in
+// registers, publishes the aggregate, looks back with a wide window (128 tiles
+// per L2 round trip: the inclusive prefixes spread from tile 0 while all tiles
+// wait) and stores the results straight from registers.
+// ---------------------------------------------------------------------------
+template <typename T, int OP, bool EXCL, bool EXT>
+__global__ void __launch_bounds__(ST) k_scan_wave(const __grid_constant__ ScanParams P) {
+  constexpr int V = 16 / sizeof(T);
+  using O = Op<OP>;
+  __shared__ T s_tot[SQ], s_off[SQ];
+  __shared__ long long s_t;
+
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
+  Slots<T> slots;
+  slots.bind(P.ws + sizeof(WsHeader), P.ntiles);
+  const unsigned tag = (ld_relaxed_u32(&hdr->epoch) & 0x3fffffffu) << 2;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T ident = O::template identity<T>();
+  T chain0 = ident, init = from_bits<T>(P.init_bits);
+  if (P.carry) {
+    if constexpr (EXCL) init = *reinterpret_cast<const T*>(P.carry);
+    else chain0 = *reinterpret_cast<const T*>(P.carry);
+  }
+  if (tid == 0) s_t = (long long)atomicAdd(&hdr->ticket, 1ull);
+  __syncthreads();
+  const long long t = s_t;
+  if (t < P.ntiles) {
+    const TileRef r = tile_ref<T, false, EXT>(P, t);
+    V16<T> xa[SCH], xb[SCH];
+    if (r.full) load_full<T>(r, false, tid, l2_policy_evict_first(), xa, xb, P.status);
+    T x[SCH][V], wexc[SCH];
+    ViewEval<T> ve;
+    tile_values<T, 0>(r, false, tid, ve, ident, xa, xb, x);
+    local_scan<T, OP, false>(x, wexc, s_tot, lane, warp, ident);
+    __syncthreads();
+    if (warp == 0) {
+      T loc[SR], exc;
+      const T agg = block_totals<T, OP>(s_tot, lane, loc, exc);
+      T prefix = chain0;
+      if (t == 0) {
+        if (lane == 0 && t != P.skip_tile) slots.publish(t, tag, kStateP, O::apply(chain0, agg));
+      } else {
+        if (lane == 0 && t != P.skip_tile) slots.publish(t, tag, kStateA, agg);
+        prefix = lookback<T, O, 4>(slots, t - 1, 0, tag, lane, P.spin_limit, P.status);
+        if (lane == 0 && t != P.skip_tile) slots.publish(t, tag, kStateP, O::apply(prefix, agg));
+      }
+      if (lane == 0) exc = ident;
+      T o = O::apply(prefix, exc);
+#pragma unroll
+      for (int q = 0; q < SR; ++q) {
+        s_off[lane * SR + q] = o;
+        o = O::apply(o, loc[q]);
+      }
+    }
+    __syncthreads();
+    char* out = r.pc->o;
+    const int64_t len = r.pc->len;
+#pragma unroll
+    for (int c = 0; c < SCH; ++c) {
+      const T pre = O::apply(s_off[c * SNW + warp], wexc[c]);
+      T y[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        if constexpr (!EXCL) y[e] = O::apply(pre, x[c][e]);
+        else y[e] = O::apply(init, e == 0 ? pre : O::apply(pre, x[c][e - 1]));
+      }
+      const int64_t off = r.base + (int64_t)(c * ST + tid) * V;
+      if (r.full) {
+        V16<T> ov;
+#pragma unroll
+        for (int e = 0; e < V; ++e) ov.v[e] = y[e];
+        char* dst = out + off * (int64_t)sizeof(T);
+        if (chk(off >= 0 && off + V <= len && ((uintptr_t)dst & 15) == 0, 106, P.status)) st16<T>(dst, ov);
+      } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+          if (off + e < len) reinterpret_cast<T*>(out)[off + e] = y[e];
+      }
+    }
+  }
+  // the last CTA restores the header for the next launch
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&hdr->done, 1u) == gridDim.x - 1) {
+      hdr->ticket = 0;
+      hdr->done = 0;
+      hdr->epoch = hdr->epoch + 1;
+      __threadfence();
+    }
+  }
+}
+
+template <typename T, int OP, int KIND, bool REV, bool EXCL, bool EXT>
 cudaError_t go(const ScanParams& p, int grid, cudaStream_t s) {
+  if constexpr (KIND == 0 && !REV) {
+    // every tile in one wave of the one-wave kernel: take it
+    static OccCache occw;
+    const int per = resident_ctas(occw, k_scan_wave<T, OP, EXCL, EXT>, ST, 0);
+    if (per > 0 && p.ntiles <= (int64_t)current_sm_count() * per) {
+      k_scan_wave<T, OP, EXCL, EXT><<<(unsigned)(p.ntiles > 0 ? p.ntiles : 1), ST, 0, s>>>(p);
+      return cudaGetLastError();
+    }
+  }
   static OccCache occ;
-  const int per_sm = resident_ctas(occ, k_scan<T, OP, KIND, REV, EXCL>, ST, smem_bytes());
+  const int per_sm = resident_ctas(occ, k_scan<T, OP, KIND, REV, EXCL, EXT>, ST, smem_bytes<KIND>());
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   if (grid <= 0) grid = current_sm_count() * per_sm;
   if (p.ntiles < grid) grid = (int)(p.ntiles > 0 ? p.ntiles : 1);
-  k_scan<T, OP, KIND, REV, EXCL><<<grid, ST, smem_bytes(), s>>>(p);
+  k_scan<T, OP, KIND, REV, EXCL, EXT><<<grid, ST, smem_bytes<KIND>(), s>>>(p);
   return cudaGetLastError();
 }
 
-template <typename T, int OP>
+template <typename T, int OP, bool EXT>
 cudaError_t dispatch_op(const ScanParams& p, int grid, cudaStream_t s) {
   // KIND 0 (a plain vector) for every operator; the interpreted view otherwise
   const bool zip = p.vc.nleaf == 2;
   if (p.exclusive) {
-    if (p.vc.kind == 0) return go<T, OP, 0, false, true>(p, grid, s);
-    return zip ? go<T, OP, 3, false, true>(p, grid, s) : go<T, OP, 2, false, true>(p, grid, s);
+    if (p.vc.kind == 0) return go<T, OP, 0, false, true, EXT>(p, grid, s);
+    return zip ? go<T, OP, 3, false, true, EXT>(p, grid, s) : go<T, OP, 2, false, true, EXT>(p, grid, s);
   }
-  if (p.vc.kind == 0) return go<T, OP, 0, false, false>(p, grid, s);
-  return zip ? go<T, OP, 3, false, false>(p, grid, s) : go<T, OP, 2, false, false>(p, grid, s);
+  if (p.vc.kind == 0) return go<T, OP, 0, false, false, EXT>(p, grid, s);
+  return zip ? go<T, OP, 3, false, false, EXT>(p, grid, s) : go<T, OP, 2, false, false, EXT>(p, grid, s);
 }
 
-template <typename T>
+// EXT: the call's piece table is in device memory (more than kMaxPieces pieces).
+template <typename T, bool EXT>
 cudaError_t dispatch(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
   if (reverse) {
-    if (p.vc.kind == 0) return go<T, DR_PLUS, 0, true, false>(p, grid, s);
-    return p.vc.nleaf == 2 ? go<T, DR_PLUS, 3, true, false>(p, grid, s) : go<T, DR_PLUS, 2, true, false>(p, grid, s);
+    if (p.vc.kind == 0) return go<T, DR_PLUS, 0, true, false, EXT>(p, grid, s);
+    return p.vc.nleaf == 2 ? go<T, DR_PLUS, 3, true, false, EXT>(p, grid, s)
+                           : go<T, DR_PLUS, 2, true, false, EXT>(p, grid, s);
   }
   switch (p.op) {
-    case DR_PLUS: return dispatch_op<T, DR_PLUS>(p, grid, s);
-    case DR_MIN: return dispatch_op<T, DR_MIN>(p, grid, s);
-    default: return dispatch_op<T, DR_MAX>(p, grid, s);
+    case DR_PLUS: return dispatch_op<T, DR_PLUS, EXT>(p, grid, s);
+    case DR_MIN: return dispatch_op<T, DR_MIN, EXT>(p, grid, s);
+    default: return dispatch_op<T, DR_MAX, EXT>(p, grid, s);
   }
 }
 

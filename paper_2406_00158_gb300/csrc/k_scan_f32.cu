@@ -3,6 +3,6 @@
 
 namespace dr {
 cudaError_t launch_scan_f32(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
-  return kscan::dispatch<float>(p, reverse, grid, s);
+  return kscan::dispatch<float, false>(p, reverse, grid, s);
 }
 }  // namespace dr

@@ -3,6 +3,6 @@
 
 namespace dr {
 cudaError_t launch_scan_f64(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
-  return kscan::dispatch<double>(p, reverse, grid, s);
+  return kscan::dispatch<double, false>(p, reverse, grid, s);
 }
 }  // namespace dr

@@ -1,0 +1,9 @@
+// scan kernels instantiated for double with the piece table in device memory (calls
+// of more than 128 pieces; one translation unit per element type).
+#include "k_scan.cuh"
+
+namespace dr {
+cudaError_t launch_scan_f64_ext(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
+  return kscan::dispatch<double, true>(p, reverse, grid, s);
+}
+}  // namespace dr

@@ -3,6 +3,6 @@
 
 namespace dr {
 cudaError_t launch_scan_i32(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
-  return kscan::dispatch<int>(p, reverse, grid, s);
+  return kscan::dispatch<int, false>(p, reverse, grid, s);
 }
 }  // namespace dr

@@ -3,6 +3,6 @@
 
 namespace dr {
 cudaError_t launch_scan_i64(const ScanParams& p, bool reverse, int grid, cudaStream_t s) {
-  return kscan::dispatch<long long>(p, reverse, grid, s);
+  return kscan::dispatch<long long, false>(p, reverse, grid, s);
 }
 }  // namespace dr

@@ -482,3 +482,16 @@ def test_strict_align_zip(lib):
     assert zip_ex([4, 4], [4, 6], S, take=6) == L.DR_OK       # aligned over the taken windows
     assert zip_ex([4, 4], [4, 6], S) == L.DR_E_ALIGN          # but not over the whole vectors
     assert zip_ex([4, 4], [4, 4], 2) == L.DR_E_INVAL
+
+
+def test_vec_rebind_validation(lib):
+    lens = [8, 0, 5]
+    _, h = make_vec(lens)
+    P = lambda ptrs: (ctypes.c_void_p * 3)(*ptrs)
+    assert lib.dr_vec_rebind(None, P([1 << 40, 0, 1 << 41])) == L.DR_E_INVAL
+    assert lib.dr_vec_rebind(h, None) == L.DR_E_INVAL
+    assert lib.dr_vec_rebind(h, P([0, 0, 1 << 41])) == L.DR_E_INVAL          # non-empty segment, NULL
+    assert lib.dr_vec_rebind(h, P([(1 << 40) + 2, 0, 1 << 41])) == L.DR_E_ALIGN
+    assert lib.dr_vec_rebind(h, P([1 << 40, 0, 1 << 41])) == L.DR_OK
+    ptr = ctypes.c_void_p()
+    assert lib.dr_vec_segment(h, 2, ctypes.byref(ptr), None, None) == 0 and ptr.value == 1 << 41

@@ -92,6 +92,23 @@ def test_scan_grad_full_size_exact_integer_valued(ag):
     assert np.array_equal(g, bwd.astype(np.float32))
 
 
+def test_scan_grad_repeated_calls_reuse_one_plan(ag):
+    """The autograd scan keeps one vector / view per shape and rebinds it to each
+    call's tensors: successive calls on new data must each be right."""
+    n = 3 * 8192 + 100
+    lens = [5000, 0, n - 5000]
+    for seed in range(3):
+        xi = inputs.uniform_int64(inputs.SEED_GRAD + 20 + seed, n, -1, 2)
+        wi = inputs.uniform_int64(inputs.SEED_GRAD + 30 + seed, n, -1, 2)
+        segs = split(torch.from_numpy(xi.astype(np.float32)).cuda(), lens)
+        ys = ag.inclusive_scan(segs)
+        torch.autograd.backward(list(ys), list(torch.from_numpy(wi.astype(np.float32)).cuda().split(lens)))
+        y = torch.cat([t.detach() for t in ys]).cpu().numpy()
+        g = torch.cat([s.grad for s in segs]).cpu().numpy()
+        assert np.array_equal(y, oracle.inclusive_scan_i64(xi).astype(np.float32))
+        assert np.array_equal(g, oracle.reverse_inclusive_scan_f64(wi.astype(np.float64)).astype(np.float32))
+
+
 @pytest.mark.parametrize("n,lx,ly", [(300, [100, 200], [300]), (1 << 22, None, None)])
 def test_dot_grad(ag, n, lx, ly):
     x = inputs.uniform_pm1_f32(51, n)

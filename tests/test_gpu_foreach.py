@@ -212,3 +212,22 @@ def test_transform_float_single_rounding_and_in_place(api):
     api.transform(vx.view().transform("square"), vx)   # in place
     api.sync_status()
     assert np.array_equal(G.to_np(vx), x * x)
+
+
+def test_for_each_follows_a_rebound_vector():
+    """for_each over a zip whose vectors were rebound to new storage writes the new storage."""
+    G.dev()
+    from paper_2406_00158_gb300 import api
+    n = 4 * 1024 + 3
+    a, b, c = inputs.stream_inputs(n, np.float64)
+    va, vb, vc = G.segvec(a, [n]), G.segvec(b, [n]), G.segvec(c, [n])
+    z = api.View.zipn(va, vb, vc)
+    a2, b2, c2 = inputs.stream_inputs(n, np.float64, key=inputs.SEED_STREAM + 10)
+    new = [G.guarded_segment(n, torch.float64) for _ in range(3)]
+    for t, v in zip(new, (a2, b2, c2)):
+        t.copy_(torch.from_numpy(v))
+    va.rebind([new[0]]), vb.rebind([new[1]]), vc.rebind([new[2]])
+    api.for_each(z, "triad", 3.0)
+    api.sync_status()
+    assert np.array_equal(new[0].cpu().numpy(), oracle.stream("triad", a2, b2, c2, 3.0)[0])
+    assert np.array_equal(va._bases[0].cpu().numpy(), a)     # the old storage was not written

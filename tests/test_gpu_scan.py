@@ -328,3 +328,26 @@ def test_scan_over_zip_view_float_within_bound(api):
     # each product is rounded once to fp32 before the scan: one more rounding per term
     bound = T.scan_bound(absref, tiles) + 2.0 ** -24 * absref
     assert np.all(np.abs(G.to_np(out).astype(np.float64) - ref) <= bound)
+
+
+@pytest.mark.parametrize("n", [3 * 8192 + 5, 700 * 8192 + 3])
+def test_scan_with_carry_inclusive_and_exclusive(api, n):
+    """dr_scan_with_carry: the chain starts from a device value (inclusive), or the
+    value is the exclusive scan's init; a small range (the one-wave kernel) and a
+    range of more tiles than one wave (the pipeline), integer-valued, exact."""
+    xi = inputs.uniform_int64(2406 + 600, n, -1, 2)
+    lens = [n // 3, 0, n - n // 3]
+    vx = G.segvec(xi.astype(np.float32), lens)
+    out = G.empty_like_vec([n], torch.float32)
+    carry = torch.tensor([17.0], device="cuda")
+    api.scan_with_carry(vx, out, carry)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), (17 + oracle.inclusive_scan_i64(xi)).astype(np.float32))
+    api.scan_with_carry(vx, out, carry, exclusive=True)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), oracle.scan(xi, "plus", exclusive=True, init=17).astype(np.float32))
+    vi = G.segvec(xi * 1000, lens)
+    o64 = G.empty_like_vec([n], torch.int64)
+    api.scan_with_carry(vi, o64, torch.tensor([-5], dtype=torch.int64, device="cuda"), op="max")
+    api.sync_status()
+    assert np.array_equal(G.to_np(o64), oracle.scan(xi * 1000, "max", init=-5))
