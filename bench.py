@@ -168,6 +168,58 @@ def cpu_oracle_run(x: np.ndarray, y: np.ndarray, reps: int) -> tuple[float, int]
     return dt, reps * x.size * (BYTES_DOT + BYTES_SCAN)
 
 
+def _oracle_core(x: np.ndarray, y: np.ndarray, reps: int, barrier, q) -> None:
+    """One host core's share of the all-cores baseline (a spawned process): the oracle
+    as it stands on its own slice of the sample, timed after every process is ready."""
+    import oracle
+    oracle.lib()
+    cpu_oracle_run(x[:1 << 16], y[:1 << 16], 1)
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    dt, nb = cpu_oracle_run(x, y, reps)
+    q.put((t0, t0 + dt, nb))
+
+
+def cpu_oracle_all_cores(x: np.ndarray, y: np.ndarray, reps: int, procs: int) -> tuple[float, int]:
+    """The oracle on every host core at once: `procs` spawned processes, each over an
+    independent slice of the sample (one dot + one scan per slice), so the figure is
+    the host's aggregate oracle throughput.  Returns (wall seconds from the first start
+    to the last finish, bytes)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(procs), ctx.Queue()
+    cut = np.linspace(0, x.size, procs + 1).astype(np.int64)
+    ps = [ctx.Process(target=_oracle_core, args=(x[cut[k]:cut[k + 1]], y[cut[k]:cut[k + 1]], reps, barrier, q))
+          for k in range(procs)]
+    for p in ps:
+        p.start()
+    import queue
+    res, deadline = [], time.monotonic() + 900
+    try:
+        while len(res) < procs:
+            try:
+                res.append(q.get(timeout=2))
+            except queue.Empty:
+                if time.monotonic() > deadline or any(p.exitcode not in (None, 0) for p in ps):
+                    raise RuntimeError("all-cores oracle baseline: a worker failed or timed out")
+    finally:
+        for p in ps:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.kill()
+    return max(r[1] for r in res) - min(r[0] for r in res), sum(r[2] for r in res)
+
+
+def cpu_stencil_f64(steps: int) -> float:
+    """Seconds for `steps` steps of the oracle's FP64 5-point stencil on the 16384^2 grid."""
+    import oracle
+    u0 = inputs.uniform01_f32(inputs.SEED_STENCIL, 16384 * 16384).reshape(16384, 16384).astype(np.float64)
+    oracle.stencil5_f64(u0[:64, :64], 1)
+    t0 = time.perf_counter()
+    oracle.stencil5_f64(u0, steps)
+    return time.perf_counter() - t0
+
+
 def run_reference(args) -> None:
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -271,6 +323,8 @@ def measure_rows(api, dev, s, peak) -> dict:
     gw = torch.ones(R, C, device=dev).split(2048)
 
     def stencil_fb():
+        for q in blocks:
+            q.grad = None
         outs = AG.stencil(blocks, 50, 0.0, 0.25, checkpoint_every=10)
         torch.autograd.backward(list(outs), list(gw))
 
@@ -358,6 +412,8 @@ def measure_rows(api, dev, s, peak) -> dict:
     gy = list(torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_GRAD + 1, n)).to(dev).split(n // 8))
 
     def scan_fb():
+        for q in xs:            # a training step's zero_grad(set_to_none=True)
+            q.grad = None
         ys = AG.inclusive_scan(xs)
         torch.autograd.backward(list(ys), gy)
 
@@ -696,6 +752,15 @@ def main() -> None:
         cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": "oracle FP64 dot + FP64 inclusive_scan over the first 2^26 elements, 2 repetitions",
                "host": {"machine": platform.machine(), "logical_cpus": os.cpu_count()}}
+        procs = os.cpu_count() or 1
+        dt, nb = cpu_oracle_all_cores(x[:sample], y[:sample], 2, procs)
+        cpu["all_cores"] = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": procs, "kind": "oracle",
+                            "sample": f"the same 2^26 elements cut into {procs} independent slices, one process "
+                                      "per core, each an oracle dot + scan of its slice, 2 repetitions"}
+        st = cpu_stencil_f64(2)
+        cpu["stencil"] = {"ms_100_steps": st / 2 * 100 * 1e3, "extrapolated_from_steps": 2, "cores": 1,
+                          "kind": "oracle", "sample": "oracle FP64 5-point stencil on 16384^2, 2 timed steps, "
+                          "extrapolated linearly to 100 steps"}
 
     rows = {}
     if not args.no_rows and D.world == 1:      # the other rows are single-GPU workloads

@@ -62,7 +62,7 @@ constexpr int kTileBytes = ST * SCH * 16;
 // more stage (the tile being reduced, the next one, and the one awaiting its S
 // phase), 96 KB per CTA at two CTAs per SM.
 template <int KIND>
-__host__ __device__ constexpr bool keeps_view() { return false && KIND == 3; }
+__host__ __device__ constexpr bool keeps_view() { return KIND == 3; }
 template <int KIND>
 __host__ __device__ constexpr int smem_stages() { return keeps_view<KIND>() ? kStages + 1 : kStages; }
 template <int KIND>
