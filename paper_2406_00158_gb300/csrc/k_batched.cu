@@ -239,8 +239,9 @@ __global__ void __launch_bounds__(THREADS) k_batch(const __grid_constant__ Batch
 //   R phase, tile t_k: x and p arrive in a shared-memory stage by two TMA bulk
 //     copies issued two iterations earlier (full tiles; ragged ones load
 //     directly), with the tile's descriptor beside them; the dot partial and the
-//     scan tree of x run, and the tile aggregate is published (the vector's
-//     first tile publishes its inclusive prefix).
+//     sum of x (a reduction: the aggregate needs no scan) run, and the tile
+//     aggregate is published (the vector's first tile publishes its inclusive
+//     prefix).
 //   S phase, tile t_{k-1}: warp 0 looks back within the vector, publishes the
 //     inclusive prefix, and the CTA re-reads x (an L2 hit), scans it with the
 //     carry and stores y.
@@ -313,6 +314,21 @@ __device__ __forceinline__ void la_local_scan(float (&x)[CH][4], float (&wexc)[C
     const float wt = __shfl_sync(0xffffffffu, wi, 31);
     if (lane == 0) s_tot[c * LNW + warp] = wt;
   }
+}
+
+// The R phase needs only the tile's aggregate: a tree over the thread's values,
+// then over the warp; one total per warp.
+template <int CH>
+__device__ __forceinline__ void la_reduce(const float (&x)[CH][4], float* s_tot, int lane, int warp) {
+  float c[CH];
+#pragma unroll
+  for (int q = 0; q < CH; ++q) c[q] = fadd(fadd(x[q][0], x[q][1]), fadd(x[q][2], x[q][3]));
+#pragma unroll
+  for (int w = CH / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) c[q] = fadd(c[q], c[q + w]);
+  const float s = warp_reduce<float, DR_PLUS>(c[0]);
+  if (lane == 0) s_tot[warp] = s;
 }
 
 template <int CH>
@@ -418,8 +434,7 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
       }
       const float dsum = warp_reduce<float, DR_PLUS>((d0 + d1) + (d2 + d3));
       if (lane == 0) s_dot[warp] = dsum;
-      float wx[CH];
-      la_local_scan<CH>(x, wx, s_totR, lane, warp);
+      la_reduce<CH>(x, s_totR, lane, warp);
     }
     if (__syncthreads_or(copy_lost)) {  // ---- barrier A: s_totR, s_dot; the R stage is read
       // A bulk copy did not complete within its bound (DR_E_TIMEOUT is recorded):
@@ -443,8 +458,7 @@ __global__ void __launch_bounds__(LT, MINB) k_batch_la(const __grid_constant__ B
     float prefix = 0.f;
     if (warp == 0) {
       if (haveR) {
-        float loc[G::SR], exc;
-        const float agg = la_block_totals<CH>(s_totR, lane, loc, exc);
+        const float agg = warp_reduce<float, DR_PLUS>(lane < LNW ? s_totR[lane] : 0.f);
         if (lane == 0) {
           W.slots.publish(t, tag, t == cur.first ? kStateP : kStateA, agg);
           s_agg = agg;

@@ -12,15 +12,16 @@
 // Iteration k of a CTA handles two tiles:
 //   R phase, tile t_k: its bytes were copied into a shared-memory stage by one
 //     TMA bulk copy (cp.async.bulk, completing on the stage's mbarrier) issued
-//     one iteration earlier; fold the view, run the thread / warp / block scan
-//     tree and publish the tile aggregate.  The freed stage is refilled with the
-//     next ticketed tile.
+//     one iteration earlier; fold the view, reduce the tile (thread, warp,
+//     block: the aggregate needs no scan) and publish the aggregate.  The freed
+//     stage is refilled with the next ticketed tile.
 //   S phase, tile t_{k-1}: warp 0 looks back over the predecessors (all of them
 //     published their aggregates at least an iteration ago, so the walk rarely
 //     waits), publishes the inclusive prefix, and the CTA re-reads the tile --
 //     mostly an L2 hit: the re-read and the output stores carry an
 //     evict_first policy so they do not push the staged tiles out -- scans it
-//     with the same tree plus the carry and stores it.
+//     (thread, warp, block; every warp scans the block's chunk totals itself)
+//     with the carry and stores it.
 // Measured on GB300 (2^28 fp32): with one tile per CTA in flight a CTA spent
 // ~1.8 us loading and ~7 us waiting in lookback for predecessors still loading;
 // the lookahead order removes most of that wait, L2 eviction policies keep the
@@ -47,7 +48,10 @@ namespace kscan {
 #ifndef DR_SCAN_LOOKBACK_G
 #define DR_SCAN_LOOKBACK_G 1
 #endif
-constexpr int ST = 256;           // threads per CTA
+#ifndef DR_SCAN_THREADS
+#define DR_SCAN_THREADS 256
+#endif
+constexpr int ST = DR_SCAN_THREADS;  // threads per CTA
 constexpr int SCH = DR_SCAN_CHUNKS;  // 16-byte chunks per thread per tile (8: 32 KB tiles)
 constexpr int SNW = ST / 32;      // warps
 constexpr int SQ = SCH * SNW;     // warp-chunk totals per tile
@@ -201,6 +205,28 @@ __device__ __forceinline__ void local_scan(T (&x)[SCH][16 / sizeof(T)], T (&wexc
   }
 }
 
+// The R phase needs only the tile's aggregate: each thread folds its values (a
+// tree), the warp folds the threads; one total per warp (ops are commutative).
+template <typename T, int OP>
+__device__ __forceinline__ void tile_reduce(const T (&x)[SCH][16 / sizeof(T)], T* s_tot, int lane, int warp) {
+  constexpr int V = 16 / sizeof(T);
+  using O = Op<OP>;
+  T c[SCH];
+#pragma unroll
+  for (int q = 0; q < SCH; ++q) {
+    T a = x[q][0];
+#pragma unroll
+    for (int e = 1; e < V; ++e) a = O::apply(a, x[q][e]);
+    c[q] = a;
+  }
+#pragma unroll
+  for (int w = SCH / 2; w >= 1; w >>= 1)
+#pragma unroll
+    for (int q = 0; q < w; ++q) c[q] = O::apply(c[q], c[q + w]);
+  const T s = warp_reduce<T, OP>(c[0]);
+  if (lane == 0) s_tot[warp] = s;
+}
+
 // Warp 0: block-level inclusive scan of the SQ totals (SR consecutive per lane).
 // Returns the tile aggregate; exc = exclusive prefix of this lane's group.
 template <typename T, int OP>
@@ -252,9 +278,9 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
   using O = Op<OP>;
   extern __shared__ __align__(128) char s_stage[];  // NST x kTileBytes
   __shared__ __align__(8) unsigned long long s_bar[NST];
-  __shared__ T s_totR[SQ], s_totS[SQ], s_off[SQ];
+  __shared__ T s_totR[SNW], s_totS[SQ];
   __shared__ long long s_tk[kStages + 1];
-  __shared__ T s_agg;
+  __shared__ T s_agg, s_pref;
 
   WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
   Slots<T> slots;
@@ -340,7 +366,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
           *reinterpret_cast<V16<T>*>(st + (c * ST + tid) * 16) = v;
         }
       }
-      local_scan<T, OP, REV>(x, wx, s_totR, lane, warp, ident);
+      tile_reduce<T, OP>(x, s_totR, lane, warp);
     }
     // the ticket after the staged ones (needed only at the end of the iteration)
     const long long tlast = tk[kStages - 1];
@@ -360,8 +386,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     T prefix = (haveS && tprev == 0) ? chain0 : ident;
     if (warp == 0) {
       if (haveR) {
-        T loc[SR], exc;
-        const T agg = block_totals<T, OP>(s_totR, lane, loc, exc);
+        const T agg = warp_reduce<T, OP>(lane < SNW ? s_totR[lane] : ident);
         if (lane == 0 && t != P.skip_tile)
           slots.publish(t, tag, t == 0 ? kStateP : kStateA, t == 0 ? O::apply(chain0, agg) : agg);
         if (lane == 0) s_agg = agg;
@@ -371,6 +396,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
         prefix = lookback<T, O, kLookbackG>(slots, tprev - 1, 0, tag, lane, P.spin_limit, P.status);
         if (lane == 0 && tprev != P.skip_tile) slots.publish(tprev, tag, kStateP, O::apply(prefix, aggprev));
       }
+      if (lane == 0) s_pref = prefix;
     }
 
     // ---- S phase: tile tprev again -- re-read from L2, or (a zip view) its view
@@ -394,22 +420,29 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
       }
       local_scan<T, OP, REV>(x, wexc, s_totS, lane, warp, ident);
       __syncthreads();
-      if (warp == 0) {
-        T loc[SR], exc;
+      // every warp scans the SQ chunk totals itself (no second barrier for a table
+      // of offsets): the carry-in of each of this thread's chunks' warp segments
+      T cbase[SCH];
+      {
+        T loc[SR], exc, offs[SR];
         block_totals<T, OP>(s_totS, lane, loc, exc);
         if (lane == 0) exc = ident;
-        T o = O::apply(prefix, exc);
+        offs[0] = O::apply(s_pref, exc);
 #pragma unroll
-        for (int r = 0; r < SR; ++r) {
-          s_off[lane * SR + r] = o;
-          o = O::apply(o, loc[r]);
+        for (int r = 1; r < SR; ++r) offs[r] = O::apply(offs[r - 1], loc[r - 1]);
+#pragma unroll
+        for (int c = 0; c < SCH; ++c) {
+          const int q = REV ? SQ - 1 - (c * SNW + warp) : c * SNW + warp;
+          T sel = offs[0];
+#pragma unroll
+          for (int r = 1; r < SR; ++r)
+            if (q % SR == r) sel = offs[r];
+          cbase[c] = __shfl_sync(0xffffffffu, sel, q / SR);
         }
       }
-      __syncthreads();
 #pragma unroll
       for (int c = 0; c < SCH; ++c) {
-        const int q = REV ? SQ - 1 - (c * SNW + warp) : c * SNW + warp;
-        const T pre = O::apply(s_off[q], wexc[c]);
+        const T pre = O::apply(cbase[c], wexc[c]);
         T y[V];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
@@ -455,7 +488,8 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     for (int d = 0; d < kStages - 1; ++d) tk[d] = tk[d + 1];
     tk[kStages - 1] = tn;
     sidx = (sidx + 1) % NST;
-    __syncthreads();
+    // no barrier here: the next writes of every shared value read since the one
+    // above come after the next iteration's first barrier
   }
 
   // ---- exit (no copy is in flight: every staged ticket left is past the end, or
