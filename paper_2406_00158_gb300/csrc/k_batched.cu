@@ -311,8 +311,7 @@ __device__ __forceinline__ void la_local_scan(float (&x)[CH][4], float (&wexc)[C
     float we = __shfl_up_sync(0xffffffffu, wi, 1);
     if (lane == 0) we = 0.f;
     wexc[c] = we;
-    const float wt = __shfl_sync(0xffffffffu, wi, 31);
-    if (lane == 0) s_tot[c * LNW + warp] = wt;
+    if (lane == 31) s_tot[c * LNW + warp] = wi;  // the lane holding the warp's total
   }
 }
 

@@ -199,9 +199,8 @@ __device__ __forceinline__ void local_scan(T (&x)[SCH][16 / sizeof(T)], T (&wexc
     T we = REV ? __shfl_down_sync(0xffffffffu, wi, 1) : __shfl_up_sync(0xffffffffu, wi, 1);
     if (lane == (REV ? 31 : 0)) we = ident;
     wexc[c] = we;
-    const T wt = __shfl_sync(0xffffffffu, wi, REV ? 0 : 31);
     const int q = REV ? SQ - 1 - (c * SNW + warp) : c * SNW + warp;
-    if (lane == 0) s_tot[q] = wt;
+    if (lane == (REV ? 0 : 31)) s_tot[q] = wi;  // the lane holding the warp's total
   }
 }
 
@@ -279,7 +278,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
   extern __shared__ __align__(128) char s_stage[];  // NST x kTileBytes
   __shared__ __align__(8) unsigned long long s_bar[NST];
   __shared__ T s_totR[SNW], s_totS[SQ];
-  __shared__ long long s_tk[kStages + 1];
+  __shared__ long long s_tk[kStages + 2];
   __shared__ T s_agg, s_pref;
 
   WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
@@ -321,6 +320,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
   long long tprev = -1;
   T aggprev = ident;  // warp 0: aggregate of tprev
   int sidx = 0;       // stage of tk[0]
+  unsigned it = 0;    // iteration parity: the s_tk slot of this iteration's ticket
 
   while (tk[0] < P.ntiles || tprev >= 0) {
     const long long t = tk[0];
@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
         tile_values<T, KIND>(rs, two, tid, ve, ident, sa, sb, x);
       }
       local_scan<T, OP, REV>(x, wexc, s_totS, lane, warp, ident);
+      if (tid == 0) s_tk[kStages + (it & 1)] = tnew;  // the next ticket, published by this barrier
       __syncthreads();
       // every warp scans the SQ chunk totals itself (no second barrier for a table
       // of offsets): the carry-in of each of this thread's chunks' warp segments
@@ -468,13 +469,17 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
         }
       }
     }
-    if (tid == 0) s_tk[kStages] = tnew;
-    __syncthreads();  // s_tk, s_agg published; shared totals free
+    if (!haveS) {  // no S-phase barrier: publish the ticket, and keep s_totR until warp 0 read it
+      if (tid == 0) s_tk[kStages + (it & 1)] = tnew;
+      __syncthreads();
+    }
     // refill the stage whose tile is done -- the one read in this R phase, or for a
     // zip view the one read in this S phase -- with the next ticketed tile (all
-    // reads of it happened before the barriers above); it is reduced two
-    // iterations from now
-    const long long tn = tlast < P.ntiles ? s_tk[kStages] : P.ntiles;
+    // reads of it happened before the last barrier); it is reduced two iterations
+    // from now.  Two barriers per iteration: s_tk is double-buffered (a slot is
+    // rewritten two iterations later, after the next iteration's first barrier)
+    const long long tn = tlast < P.ntiles ? s_tk[kStages + (it & 1)] : P.ntiles;
+    ++it;
     const int fill = (sidx + kStages) % NST;
     if (tid == 0) {
       fence_proxy_async_smem();
@@ -488,8 +493,8 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     for (int d = 0; d < kStages - 1; ++d) tk[d] = tk[d + 1];
     tk[kStages - 1] = tn;
     sidx = (sidx + 1) % NST;
-    // no barrier here: the next writes of every shared value read since the one
-    // above come after the next iteration's first barrier
+    // no barrier here: every shared value read since the last barrier is next
+    // written after the next iteration's first barrier
   }
 
   // ---- exit (no copy is in flight: every staged ticket left is past the end, or
@@ -511,15 +516,16 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
 // CTAs (e.g. 2^20 int64 = 256 tiles).  Every tile is in flight at once, so the
 // lookahead pipeline above only adds latency (a bulk copy, a second ticket, a
 // re-read of the tile); here a CTA takes one ticket, keeps its tile in
-// registers, publishes the aggregate, looks back with a wide window (128 tiles
-// per L2 round trip: the inclusive prefixes spread from tile 0 while all tiles
-// wait) and stores the results straight from registers.
+// registers, publishes the aggregate, folds the aggregates of all its
+// predecessors (every thread polls one or two of them: one L2 round trip, where
+// a lookback would wait for inclusive prefixes to spread from tile 0) and stores
+// the results straight from registers.
 // ---------------------------------------------------------------------------
 template <typename T, int OP, bool EXCL, bool EXT>
 __global__ void __launch_bounds__(ST) k_scan_wave(const __grid_constant__ ScanParams P) {
   constexpr int V = 16 / sizeof(T);
   using O = Op<OP>;
-  __shared__ T s_tot[SQ], s_off[SQ];
+  __shared__ T s_tot[SQ], s_red[SNW];
   __shared__ long long s_t;
 
   WsHeader* hdr = reinterpret_cast<WsHeader*>(P.ws);
@@ -545,31 +551,44 @@ __global__ void __launch_bounds__(ST) k_scan_wave(const __grid_constant__ ScanPa
     tile_values<T, 0>(r, false, tid, ve, ident, xa, xb, x);
     local_scan<T, OP, false>(x, wexc, s_tot, lane, warp, ident);
     __syncthreads();
-    if (warp == 0) {
-      T loc[SR], exc;
-      const T agg = block_totals<T, OP>(s_tot, lane, loc, exc);
-      T prefix = chain0;
-      if (t == 0) {
-        if (lane == 0 && t != P.skip_tile) slots.publish(t, tag, kStateP, O::apply(chain0, agg));
-      } else {
-        if (lane == 0 && t != P.skip_tile) slots.publish(t, tag, kStateA, agg);
-        prefix = lookback<T, O, 4>(slots, t - 1, 0, tag, lane, P.spin_limit, P.status);
-        if (lane == 0 && t != P.skip_tile) slots.publish(t, tag, kStateP, O::apply(prefix, agg));
-      }
-      if (lane == 0) exc = ident;
-      T o = O::apply(prefix, exc);
+    // every warp scans the chunk totals (the same order in each); thread 0
+    // publishes the aggregate (tile 0's with the carry-in folded in)
+    T loc[SR], exc;
+    const T agg = block_totals<T, OP>(s_tot, lane, loc, exc);
+    if (tid == 0 && t != P.skip_tile) slots.publish(t, tag, kStateA, t == 0 ? O::apply(chain0, agg) : agg);
+    // the carry: the fold of every predecessor's aggregate, all of them polled at
+    // once by the whole CTA (one L2 round trip, no chain of inclusive prefixes)
+    T part = ident;
+    for (long long i = tid; i < t; i += ST) {
+      T v;
+      wait_slot<T, Slots<T>, O>(slots, t - 1 - i, tag, v, P.spin_limit, P.status);
+      part = O::apply(part, v);
+    }
+    part = warp_reduce<T, OP>(part);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    const T prefix = t == 0 ? chain0 : warp_reduce<T, OP>(lane < SNW ? s_red[lane] : ident);
+    T cbase[SCH];
+    {
+      T offs[SR];
+      offs[0] = O::apply(prefix, lane == 0 ? ident : exc);
 #pragma unroll
-      for (int q = 0; q < SR; ++q) {
-        s_off[lane * SR + q] = o;
-        o = O::apply(o, loc[q]);
+      for (int q = 1; q < SR; ++q) offs[q] = O::apply(offs[q - 1], loc[q - 1]);
+#pragma unroll
+      for (int c = 0; c < SCH; ++c) {
+        const int q = c * SNW + warp;
+        T sel = offs[0];
+#pragma unroll
+        for (int k = 1; k < SR; ++k)
+          if (q % SR == k) sel = offs[k];
+        cbase[c] = __shfl_sync(0xffffffffu, sel, q / SR);
       }
     }
-    __syncthreads();
     char* out = r.pc->o;
     const int64_t len = r.pc->len;
 #pragma unroll
     for (int c = 0; c < SCH; ++c) {
-      const T pre = O::apply(s_off[c * SNW + warp], wexc[c]);
+      const T pre = O::apply(cbase[c], wexc[c]);
       T y[V];
 #pragma unroll
       for (int e = 0; e < V; ++e) {

@@ -34,6 +34,14 @@ namespace {
 #ifndef DR_SORT_ITEMS
 #define DR_SORT_ITEMS 16
 #endif
+#ifndef DR_SORT_MINB
+#define DR_SORT_MINB 4  // resident CTAs per SM the scatter is compiled for (0: no bound)
+#endif
+#if DR_SORT_MINB > 0
+#define DR_SORT_SCATTER_BOUNDS __launch_bounds__(ST, DR_SORT_MINB)
+#else
+#define DR_SORT_SCATTER_BOUNDS __launch_bounds__(ST)
+#endif
 constexpr int ST = DR_SORT_THREADS;  // threads per CTA (a multiple of 256)
 constexpr int SW = ST / 32;
 constexpr int RADIX = 256;           // threads < RADIX own one digit in the digit phases
@@ -139,7 +147,10 @@ __device__ __forceinline__ T view_elem(const KPiece& pc, int64_t j, const ViewEv
 // carry the digit RADIX), or match.any (DR_SORT_MATCH=1).  Measured on GB300,
 // 2^28 fp32 keys: ballots 7.5 ms, match.any 9.0 ms (its latency, not the
 // issue slots, bounds the ranking).  Shapes: 256 x 16 and 512 x 12 tie; 1024
-// threads and 24 items per thread are slower.
+// threads and 24 items per thread are slower.  The scatter compiled for 4 CTAs per
+// SM (64 registers) beats 3 (78 registers) by 2 %; 12 or 8 items per thread at 4 or
+// 6 CTAs per SM are slower (6.17, 6.91 ms against 5.98 ms for 2^28 fp32 keys), and
+// match.any at 4 CTAs per SM takes 7.6 ms.
 #ifndef DR_SORT_MATCH
 #define DR_SORT_MATCH 0
 #endif
@@ -265,7 +276,7 @@ __global__ void __launch_bounds__(ST) k_sort_count(const __grid_constant__ SortP
 // to the output segments (last pass).
 // ---------------------------------------------------------------------------
 template <typename T, int SRC, int DST>
-__global__ void __launch_bounds__(ST) k_sort_scatter(const __grid_constant__ SortParams P) {
+__global__ void DR_SORT_SCATTER_BOUNDS k_sort_scatter(const __grid_constant__ SortParams P) {
   using KO = KeyOf<T>;
   using K = typename KO::K;
   constexpr int SIT = Tile<sizeof(K)>::IT, STILE = Tile<sizeof(K)>::N;
