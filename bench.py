@@ -419,7 +419,17 @@ def measure_rows(api, dev, s, peak) -> dict:
 
     ms = _time(scan_fb, s, 10)
     rows["autograd_scan_2^26_8segs_fwd+bwd"] = _row(ms, 16 * n, peak)
-    del xs, gy
+    # the same through the one-tensor variant (one autograd node: less host work)
+    xf = torch.cat([q.detach() for q in xs]).requires_grad_(True)
+    gf = torch.cat(gy)
+
+    def scan_flat_fb():
+        xf.grad = None
+        AG.inclusive_scan_flat(xf, [n // 8] * 8).backward(gf)
+
+    ms = _time(scan_flat_fb, s, 10)
+    rows["autograd_scan_flat_2^26_8segs_fwd+bwd"] = _row(ms, 16 * n, peak)
+    del xs, gy, xf, gf
 
     # batched: 4096 vectors, log-uniform [1e3, 1e6], 1-8 segments; one launch vs one per range
     shapes = inputs.batch_shapes(inputs.SEED_BATCH, 4096)

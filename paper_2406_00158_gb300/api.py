@@ -114,6 +114,18 @@ class SegmentedVector:
         self.segments = segs
         return self
 
+    def _rebind_unchecked(self, segs: list) -> None:
+        """rebind() for tensors the caller already made 1-D, contiguous and of
+        this vector's lengths and dtype (the autograd plans): one pointer array
+        reused, no Python-side checks (the library still checks the pointers)."""
+        arr = getattr(self, "_ptrs", None)
+        if arr is None:
+            arr = self._ptrs = (ctypes.c_void_p * len(self._lens))()
+        for i, t in enumerate(segs):
+            arr[i] = t.data_ptr()
+        call("dr_vec_rebind", self.handle, arr)
+        self.segments = segs
+
     @property
     def n(self) -> int:
         return sum(s.numel() for s in self.segments)

@@ -26,11 +26,17 @@ def _contig(ts):
     return [t.contiguous() for t in ts]
 
 
+_ESZ = {torch.float32: 4, torch.float64: 8, torch.int32: 4, torch.int64: 8}
+
+
 def _segments_like(lens, dtype, device):
     """Output segments in one allocation, each starting on a 16-byte boundary
     (so the kernels keep their 128-bit path)."""
-    esz = torch.empty((), dtype=dtype).element_size()
-    a = 16 // esz
+    a = 16 // _ESZ.get(dtype, 16)
+    if a and all(n % a == 0 for n in lens) and sum(lens) > 0:
+        # every length keeps the next segment aligned: one split, no padding
+        return list(torch.empty(sum(lens), dtype=dtype, device=device).split_with_sizes(lens))
+    a = max(a, 1)
     offs, pos = [], 0
     for n in lens:
         offs.append(pos)
@@ -51,8 +57,10 @@ class _Plan:
         self.y = api.SegmentedVector(ys)
 
     def bind(self, xs, ys):
-        self.x.rebind(xs)
-        self.y.rebind(ys)
+        # xs are contiguous 1-D tensors of the plan's lengths (the key guarantees
+        # lengths, dtype and device), ys come from _segments_like
+        self.x._rebind_unchecked(xs)
+        self.y._rebind_unchecked(ys)
 
     def release(self):
         # drop this call's tensors (launches already made keep their storage)
@@ -104,6 +112,37 @@ class _ScanFn(torch.autograd.Function):
 def inclusive_scan(segments: Sequence[torch.Tensor]) -> tuple:
     """Differentiable segmented inclusive scan: one output tensor per segment."""
     return _ScanFn.apply(*segments)
+
+
+class _ScanFlatFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, lens):
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        p = _plan("scan_flat", list(x.split_with_sizes(lens)), list(y.split_with_sizes(lens)))
+        api.inclusive_scan(p.view, p.y)
+        p.release()
+        ctx.lens = lens
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        gy = gy.contiguous()
+        gx = torch.empty_like(gy)
+        p = _plan("reverse_scan_flat", list(gy.split_with_sizes(ctx.lens)), list(gx.split_with_sizes(ctx.lens)))
+        api.reverse_inclusive_scan(p.view, p.y)
+        p.release()
+        return gx, None
+
+
+def inclusive_scan_flat(x: torch.Tensor, lens: Sequence[int]) -> torch.Tensor:
+    """The same scan over one flat tensor whose consecutive pieces of the given
+    lengths are the segments (one autograd node with one input and one output,
+    instead of one tensor per segment)."""
+    lens = [int(n) for n in lens]
+    if x.dim() != 1 or sum(lens) != x.numel():
+        raise ValueError("inclusive_scan_flat: x must be 1-D with sum(lens) elements")
+    return _ScanFlatFn.apply(x, lens)
 
 
 class _DotFn(torch.autograd.Function):

@@ -109,6 +109,41 @@ def test_scan_grad_repeated_calls_reuse_one_plan(ag):
         assert np.array_equal(g, oracle.reverse_inclusive_scan_f64(wi.astype(np.float64)).astype(np.float32))
 
 
+def test_scan_flat_full_size_exact_integer_valued(ag):
+    """The one-tensor variant (segments = consecutive pieces of one flat tensor):
+    2^26 in 8 segments, integer-valued walks, bit-exact forward and gradient."""
+    n = 1 << 26
+    lens = inputs.block_segments(n, 8)
+    xi = inputs.uniform_int64(inputs.SEED_GRAD + 9, n, -1, 2)
+    wi = inputs.uniform_int64(inputs.SEED_GRAD + 10, n, -1, 2)
+    fwd = oracle.inclusive_scan_i64(xi)
+    for walk in (fwd, oracle.inclusive_scan_i64(wi)):
+        assert max(int(walk.max()), 0) - min(int(walk.min()), 0) < (1 << 24)
+    x = torch.from_numpy(xi.astype(np.float32)).cuda().requires_grad_(True)
+    y = ag.inclusive_scan_flat(x, lens)
+    y.backward(torch.from_numpy(wi.astype(np.float32)).cuda())
+    assert np.array_equal(y.detach().cpu().numpy(), fwd.astype(np.float32))
+    assert np.array_equal(x.grad.cpu().numpy(),
+                          oracle.reverse_inclusive_scan_f64(wi.astype(np.float64)).astype(np.float32))
+
+
+def test_scan_flat_ragged_segments_repeated(ag):
+    """Segment lengths that leave later segments off the 16-byte grid (the
+    kernels' scalar path for those pieces), an empty segment, and two calls on
+    new data through the same cached plan."""
+    n = 5 * 8192 + 333
+    lens = [1001, 0, 4099, 7, n - 1001 - 4099 - 7]
+    for seed in range(2):
+        xi = inputs.uniform_int64(inputs.SEED_GRAD + 40 + seed, n, -1, 2)
+        wi = inputs.uniform_int64(inputs.SEED_GRAD + 50 + seed, n, -1, 2)
+        x = torch.from_numpy(xi.astype(np.float32)).cuda().requires_grad_(True)
+        y = ag.inclusive_scan_flat(x, lens)
+        y.backward(torch.from_numpy(wi.astype(np.float32)).cuda())
+        assert np.array_equal(y.detach().cpu().numpy(), oracle.inclusive_scan_i64(xi).astype(np.float32))
+        assert np.array_equal(x.grad.cpu().numpy(),
+                              oracle.reverse_inclusive_scan_f64(wi.astype(np.float64)).astype(np.float32))
+
+
 @pytest.mark.parametrize("n,lx,ly", [(300, [100, 200], [300]), (1 << 22, None, None)])
 def test_dot_grad(ag, n, lx, ly):
     x = inputs.uniform_pm1_f32(51, n)
