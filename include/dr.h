@@ -119,13 +119,14 @@ int dr_sync_status(dr_stream_t stream);
 
 /* Tile geometry of a kernel family (host only; no device needed):
  *   *tile_elems = the elements of `dtype` one tile covers -- the unit of the
- *     scan's carry chain (one lookback hop per tile), of the reduce's
+ *     scan's carry chain (one lookback hop per tile; DR_K_SCAN_VIEW: the scan
+ *     of a fused view -- ops or a zip -- whose tiles are shorter), of the reduce's
  *     per-thread accumulation, of for_each / transform and of a sort pass;
  *   *ctas_per_sm = the CTAs per SM of the kernel's grid when it is fixed by
  *     design (the reduce: its grid fixes the summation tree), else 0 (a
  *     persistent grid sized by occupancy).
  * Either output may be NULL.  Rounding-error bounds are derived from these. */
-enum dr_kernel_family { DR_K_SCAN = 0, DR_K_REDUCE = 1, DR_K_FOREACH = 2, DR_K_SORT = 3 };
+enum dr_kernel_family { DR_K_SCAN = 0, DR_K_REDUCE = 1, DR_K_FOREACH = 2, DR_K_SORT = 3, DR_K_SCAN_VIEW = 4 };
 int dr_kernel_geometry(int kernel, int dtype, int64_t* tile_elems, int* ctas_per_sm);
 
 /* Upper bound on the polls of every device-side wait (scan lookback, batched

@@ -26,7 +26,7 @@ DR_PLUS, DR_MUL, DR_MIN, DR_MAX = range(4)
 # enum dr_unop
 DR_U_SCALE, DR_U_ADD, DR_U_NEG, DR_U_ABS, DR_U_SQUARE = range(5)
 # enum dr_kernel_family
-DR_K_SCAN, DR_K_REDUCE, DR_K_FOREACH, DR_K_SORT = range(4)
+DR_K_SCAN, DR_K_REDUCE, DR_K_FOREACH, DR_K_SORT, DR_K_SCAN_VIEW = range(5)
 DR_ZIP_STRICT_ALIGN = 1
 # enum dr_rows_part
 DR_ROWS_ALL, DR_ROWS_INNER, DR_ROWS_OUTER = range(3)

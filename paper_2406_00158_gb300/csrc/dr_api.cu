@@ -286,6 +286,7 @@ extern "C" int dr_kernel_geometry(int kernel, int dtype, int64_t* tile_elems, in
   int per = 0;
   switch (kernel) {
     case DR_K_SCAN: t = scan_tile_elems(dtype); break;
+    case DR_K_SCAN_VIEW: t = scan_tile_elems(dtype, true); break;
     case DR_K_REDUCE:
       t = reduce_tile_elems(dtype);
       per = reduce_ctas_per_sm();
@@ -785,7 +786,10 @@ static int do_scan(const char* who, const dr_view* in_c, dr_vec* out, int op, bo
   p.op = op;
   p.dtype = in->dtype;
   p.exclusive = exclusive ? 1 : 0;
-  if (int r = call_pieces(in, out, scan_tile_elems(in->dtype), p.pc, &p.pc_ext, &p.npieces, &p.ntiles, s)) return r;
+  // the kernels the dispatch picks for a fused view (vc.kind != 0) have shorter tiles
+  const bool fused = p.vc.kind != 0;
+  if (int r = call_pieces(in, out, scan_tile_elems(in->dtype, fused), p.pc, &p.pc_ext, &p.npieces, &p.ntiles, s))
+    return r;
   if (int r = in->ws_scan.ensure(scan_ws_bytes(p.ntiles, in->dtype), s)) return r;
   p.ws = static_cast<char*>(in->ws_scan.ptr);
   p.status = status_word();

@@ -595,7 +595,9 @@ int resident_ctas(OccCache& c, K* kernel, int threads, int dyn_smem) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   std::lock_guard<std::mutex> g(c.mu);
   if (!c.per_sm[dev]) {
-    if (dyn_smem > 48 * 1024 &&
+    // the opt-in is needed once static + dynamic shared memory passes 48 KB, so
+    // any kernel with dynamic shared memory sets it (to exactly what it launches with)
+    if (dyn_smem > 0 &&
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem) != cudaSuccess)
       return 0;
     int per = 0;

@@ -214,7 +214,8 @@ struct HaloParams {
 
 // Tile geometry (elements per tile) of each kernel family for a dtype.
 int reduce_tile_elems(int dtype);
-int scan_tile_elems(int dtype);
+// view: the scan of a fused view (ops or a zip; its kernels' tiles are shorter)
+int scan_tile_elems(int dtype, bool view = false);
 int scale_tile_elems();
 int foreach_tile_elems(int dtype);  // for_each and transform
 int sort_tile_elems(int dtype);

@@ -20,7 +20,10 @@ cudaError_t launch_reduce_i32(const ReduceParams& p, int grid, cudaStream_t s);
 
 static bool is4(int dtype) { return dtype == DR_F32 || dtype == DR_I32; }
 
-int scan_tile_elems(int dtype) { return is4(dtype) ? kscan::stile<float>() : kscan::stile<double>(); }
+int scan_tile_elems(int dtype, bool view) {
+  if (view) return is4(dtype) ? kscan::stile<float, kscan::kViewChunks>() : kscan::stile<double, kscan::kViewChunks>();
+  return is4(dtype) ? kscan::stile<float>() : kscan::stile<double>();
+}
 
 size_t scan_ws_bytes(int64_t ntiles, int dtype) {
   return sizeof(WsHeader) + (is4(dtype) ? Slots<float>::bytes(ntiles) : Slots<double>::bytes(ntiles));

@@ -51,6 +51,9 @@ namespace kscan {
 #ifndef DR_SCAN_THREADS
 #define DR_SCAN_THREADS 256
 #endif
+#ifndef DR_SCAN_VIEW_CHUNKS
+#define DR_SCAN_VIEW_CHUNKS 4
+#endif
 constexpr int ST = DR_SCAN_THREADS;  // threads per CTA
 constexpr int SCH = DR_SCAN_CHUNKS;  // 16-byte chunks per thread per tile (8: 32 KB tiles)
 constexpr int SNW = ST / 32;      // warps
@@ -60,22 +63,35 @@ constexpr int kLookbackG = DR_SCAN_LOOKBACK_G;  // lookback slots per lane per r
 constexpr int kMinBlocks = DR_SCAN_MINB;        // resident CTAs per SM
 constexpr int kStages = 2;        // tiles ticketed ahead: the tile being reduced + the next
 constexpr int kTileBytes = ST * SCH * 16;
+constexpr int kViewChunks = DR_SCAN_VIEW_CHUNKS;  // chunks per thread of a fused view's tile
+static_assert(SQ % 32 == 0, "block-level scan assumes a multiple of 32 totals");
 
-// A zip view (KIND 3) keeps the view's values of a reduced tile in its stage
-// until the tile's S phase, instead of re-reading both leaves from L2: one
-// more stage (the tile being reduced, the next one, and the one awaiting its S
-// phase), 96 KB per CTA at two CTAs per SM.
+// Tile geometry for CH 16-byte chunks per thread.
+template <int CH>
+struct Geo {
+  static constexpr int SQ = CH * SNW;        // warp-chunk totals per tile
+  static constexpr int SR = SQ / 32;         // totals per lane in the block scan
+  static constexpr int TB = ST * CH * 16;    // tile bytes
+  static_assert(SQ % 32 == 0, "block-level scan assumes a multiple of 32 totals");
+};
+
+// A fused view (KIND 2, 3) keeps the view's values of a reduced tile in its
+// stage until the tile's S phase, instead of re-reading its leaves from L2 and
+// evaluating the view again: one more stage (the tile being reduced, the next
+// one, and the one awaiting its S phase).  Its tiles are half as long (16 KB),
+// so the three stages (48 KB) let three CTAs share an SM, as for plain vectors.
 template <int KIND>
-__host__ __device__ constexpr bool keeps_view() { return KIND == 3; }
+__host__ __device__ constexpr int chunks() { return KIND != 0 ? kViewChunks : SCH; }
+template <int KIND>
+__host__ __device__ constexpr bool keeps_view() { return KIND != 0; }
 template <int KIND>
 __host__ __device__ constexpr int smem_stages() { return keeps_view<KIND>() ? kStages + 1 : kStages; }
 template <int KIND>
-__host__ __device__ constexpr int smem_bytes() { return smem_stages<KIND>() * kTileBytes; }
-static_assert(SQ % 32 == 0, "block-level scan assumes a multiple of 32 totals");
+__host__ __device__ constexpr int smem_bytes() { return smem_stages<KIND>() * Geo<chunks<KIND>()>::TB; }
 
-template <typename T>
+template <typename T, int CH = SCH>
 __host__ __device__ constexpr int stile() {
-  return ST * SCH * (16 / (int)sizeof(T));
+  return ST * CH * (16 / (int)sizeof(T));
 }
 
 __device__ __forceinline__ int find_piece(const KPiece* pc, int n, int64_t tile) {
@@ -106,25 +122,25 @@ struct TileRef {
   bool full;     // a whole, 16-byte aligned tile: 128-bit path
 };
 
-template <typename T, bool REV, bool EXT>
+template <typename T, bool REV, bool EXT, int CH = SCH>
 __device__ __forceinline__ TileRef tile_ref(const ScanParams& P, long long lt) {
   const KPiece* tab = piece_table<EXT>(P);
   const int64_t pt = REV ? P.ntiles - 1 - lt : lt;
   const int k = find_piece(tab, P.npieces, pt);
   const KPiece* pc = &tab[k];
-  const int64_t base = (pt - pc->tile_begin) * stile<T>();
+  const int64_t base = (pt - pc->tile_begin) * stile<T, CH>();
   const bool ok = chk(lt >= 0 && lt < P.ntiles && k >= 0 && k < P.npieces && base >= 0 && base < pc->len, 100,
                       P.status);
-  return TileRef{pc, base, ok && pc->vec_ok && pc->len - base >= stile<T>()};
+  return TileRef{pc, base, ok && pc->vec_ok && pc->len - base >= stile<T, CH>()};
 }
 
 // 128-bit loads of a full tile (operand a, and b for a two-leaf view).
-template <typename T>
+template <typename T, int CH = SCH>
 __device__ __forceinline__ void load_full(const TileRef& r, bool two, int tid, unsigned long long pol,
-                                          V16<T> (&xa)[SCH], V16<T> (&xb)[SCH], unsigned* status = nullptr) {
+                                          V16<T> (&xa)[CH], V16<T> (&xb)[CH], unsigned* status = nullptr) {
   constexpr int V = 16 / sizeof(T);
 #pragma unroll
-  for (int c = 0; c < SCH; ++c) {
+  for (int c = 0; c < CH; ++c) {
     const int64_t e0 = r.base + (int64_t)(c * ST + tid) * V;
     const char* src = r.pc->a + e0 * (int64_t)sizeof(T);
     if (chk(e0 >= 0 && e0 + V <= r.pc->len && ((uintptr_t)src & 15) == 0, 104, status))
@@ -132,21 +148,21 @@ __device__ __forceinline__ void load_full(const TileRef& r, bool two, int tid, u
   }
   if (two) {
 #pragma unroll
-    for (int c = 0; c < SCH; ++c)
+    for (int c = 0; c < CH; ++c)
       xb[c] = ld16_hint<T>(r.pc->b + (r.base + (int64_t)(c * ST + tid) * V) * (int64_t)sizeof(T), pol);
   }
 }
 
 // The tile's view values in registers: from the raw 128-bit loads of a full
 // tile, or element by element (identity past the end) for a ragged one.
-template <typename T, int KIND, typename VE>
+template <typename T, int KIND, int CH, typename VE>
 __device__ __forceinline__ void tile_values(const TileRef& r, bool two, int tid, const VE& ve, T ident,
-                                            const V16<T> (&xa)[SCH], const V16<T> (&xb)[SCH],
-                                            T (&x)[SCH][16 / sizeof(T)]) {
+                                            const V16<T> (&xa)[CH], const V16<T> (&xb)[CH],
+                                            T (&x)[CH][16 / sizeof(T)]) {
   constexpr int V = 16 / sizeof(T);
   if (r.full) {
 #pragma unroll
-    for (int c = 0; c < SCH; ++c) {
+    for (int c = 0; c < CH; ++c) {
       T y[V];
 #pragma unroll
       for (int e = 0; e < V; ++e) {
@@ -157,7 +173,7 @@ __device__ __forceinline__ void tile_values(const TileRef& r, bool two, int tid,
     }
   } else {
 #pragma unroll
-    for (int c = 0; c < SCH; ++c)
+    for (int c = 0; c < CH; ++c)
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         const int64_t idx = r.base + (int64_t)(c * ST + tid) * V + e;
@@ -175,14 +191,15 @@ __device__ __forceinline__ void tile_values(const TileRef& r, bool two, int tid,
 // Thread-local and warp scans of a tile in the scan direction; warp totals go
 // to s_tot in scan order.  The same tree runs in the R and the S phase, so the
 // published aggregate equals the tile's last output exactly.
-template <typename T, int OP, bool REV>
-__device__ __forceinline__ void local_scan(T (&x)[SCH][16 / sizeof(T)], T (&wexc)[SCH], T* s_tot, int lane,
+template <typename T, int OP, bool REV, int CH = SCH>
+__device__ __forceinline__ void local_scan(T (&x)[CH][16 / sizeof(T)], T (&wexc)[CH], T* s_tot, int lane,
                                            int warp, T ident) {
   constexpr int V = 16 / sizeof(T);
+  constexpr int Q = Geo<CH>::SQ;
   using O = Op<OP>;
-  T tsum[SCH];
+  T tsum[CH];
 #pragma unroll
-  for (int c = 0; c < SCH; ++c) {
+  for (int c = 0; c < CH; ++c) {
     if constexpr (!REV) {
 #pragma unroll
       for (int e = 1; e < V; ++e) x[c][e] = O::apply(x[c][e - 1], x[c][e]);
@@ -194,32 +211,32 @@ __device__ __forceinline__ void local_scan(T (&x)[SCH][16 / sizeof(T)], T (&wexc
     }
   }
 #pragma unroll
-  for (int c = 0; c < SCH; ++c) {
+  for (int c = 0; c < CH; ++c) {
     const T wi = warp_inclusive<T, OP, REV>(tsum[c], lane);
     T we = REV ? __shfl_down_sync(0xffffffffu, wi, 1) : __shfl_up_sync(0xffffffffu, wi, 1);
     if (lane == (REV ? 31 : 0)) we = ident;
     wexc[c] = we;
-    const int q = REV ? SQ - 1 - (c * SNW + warp) : c * SNW + warp;
+    const int q = REV ? Q - 1 - (c * SNW + warp) : c * SNW + warp;
     if (lane == (REV ? 0 : 31)) s_tot[q] = wi;  // the lane holding the warp's total
   }
 }
 
 // The R phase needs only the tile's aggregate: each thread folds its values (a
 // tree), the warp folds the threads; one total per warp (ops are commutative).
-template <typename T, int OP>
-__device__ __forceinline__ void tile_reduce(const T (&x)[SCH][16 / sizeof(T)], T* s_tot, int lane, int warp) {
+template <typename T, int OP, int CH = SCH>
+__device__ __forceinline__ void tile_reduce(const T (&x)[CH][16 / sizeof(T)], T* s_tot, int lane, int warp) {
   constexpr int V = 16 / sizeof(T);
   using O = Op<OP>;
-  T c[SCH];
+  T c[CH];
 #pragma unroll
-  for (int q = 0; q < SCH; ++q) {
+  for (int q = 0; q < CH; ++q) {
     T a = x[q][0];
 #pragma unroll
     for (int e = 1; e < V; ++e) a = O::apply(a, x[q][e]);
     c[q] = a;
   }
 #pragma unroll
-  for (int w = SCH / 2; w >= 1; w >>= 1)
+  for (int w = CH / 2; w >= 1; w >>= 1)
 #pragma unroll
     for (int q = 0; q < w; ++q) c[q] = O::apply(c[q], c[q + w]);
   const T s = warp_reduce<T, OP>(c[0]);
@@ -228,14 +245,15 @@ __device__ __forceinline__ void tile_reduce(const T (&x)[SCH][16 / sizeof(T)], T
 
 // Warp 0: block-level inclusive scan of the SQ totals (SR consecutive per lane).
 // Returns the tile aggregate; exc = exclusive prefix of this lane's group.
-template <typename T, int OP>
-__device__ __forceinline__ T block_totals(const T* s_tot, int lane, T (&loc)[SR], T& exc) {
+template <typename T, int OP, int CH = SCH>
+__device__ __forceinline__ T block_totals(const T* s_tot, int lane, T (&loc)[Geo<CH>::SR], T& exc) {
   using O = Op<OP>;
-  T lsum = s_tot[lane * SR];
+  constexpr int R = Geo<CH>::SR;
+  T lsum = s_tot[lane * R];
   loc[0] = lsum;
 #pragma unroll
-  for (int r = 1; r < SR; ++r) {
-    loc[r] = s_tot[lane * SR + r];
+  for (int r = 1; r < R; ++r) {
+    loc[r] = s_tot[lane * R + r];
     lsum = O::apply(lsum, loc[r]);
   }
   const T inc = warp_inclusive<T, OP, false>(lsum, lane);
@@ -249,15 +267,16 @@ __device__ __forceinline__ T block_totals(const T* s_tot, int lane, T (&loc)[SR]
 // a stage's barrier phase counts its uses.
 // With two leaves (a zip view), the tile's range of leaf b is prefetched into
 // L2 at the same time, so the R phase's loads of b hit L2.
-template <typename T, bool REV, bool EXT>
+template <typename T, bool REV, bool EXT, int CH = SCH>
 __device__ __forceinline__ void stage_issue(const ScanParams& P, long long lt, char* stage,
                                             unsigned long long* bar, bool two = false) {
+  constexpr int TB = Geo<CH>::TB;
   if (lt < P.ntiles) {
-    const TileRef r = tile_ref<T, REV, EXT>(P, lt);
+    const TileRef r = tile_ref<T, REV, EXT, CH>(P, lt);
     if (r.full) {
-      mbar_expect_tx(bar, kTileBytes);
-      bulk_g2s(stage, r.pc->a + r.base * (int64_t)sizeof(T), kTileBytes, bar);
-      if (two) bulk_prefetch_l2(r.pc->b + r.base * (int64_t)sizeof(T), kTileBytes);
+      mbar_expect_tx(bar, TB);
+      bulk_g2s(stage, r.pc->a + r.base * (int64_t)sizeof(T), TB, bar);
+      if (two) bulk_prefetch_l2(r.pc->b + r.base * (int64_t)sizeof(T), TB);
       return;
     }
   }
@@ -270,14 +289,16 @@ __device__ __forceinline__ void stage_issue(const ScanParams& P, long long lt, c
 // REV: scan from the last element to the first (reverse inclusive scan).
 // EXCL: exclusive scan with init.
 template <typename T, int OP, int KIND, bool REV, bool EXCL, bool EXT>
-__global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
+__global__ void __launch_bounds__(ST, kMinBlocks) k_scan(const __grid_constant__ ScanParams P) {
   constexpr int V = 16 / sizeof(T);
   constexpr bool KEEP = keeps_view<KIND>();
   constexpr int NST = smem_stages<KIND>();
+  constexpr int CH = chunks<KIND>();        // 16-byte chunks per thread per tile
+  constexpr int TB = Geo<CH>::TB, Q = Geo<CH>::SQ, R = Geo<CH>::SR;
   using O = Op<OP>;
-  extern __shared__ __align__(128) char s_stage[];  // NST x kTileBytes
+  extern __shared__ __align__(128) char s_stage[];  // NST x TB
   __shared__ __align__(8) unsigned long long s_bar[NST];
-  __shared__ T s_totR[SNW], s_totS[SQ];
+  __shared__ T s_totR[SNW], s_totS[Q];
   __shared__ long long s_tk[kStages + 2];
   __shared__ T s_agg, s_pref;
 
@@ -308,7 +329,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     fence_mbar_init();
     for (int d = 0; d < kStages; ++d) {
       s_tk[d] = (long long)atomicAdd(&hdr->ticket, 1ull);
-      stage_issue<T, REV, EXT>(P, s_tk[d], s_stage + d * kTileBytes, &s_bar[d], two);
+      stage_issue<T, REV, EXT, CH>(P, s_tk[d], s_stage + d * TB, &s_bar[d], two);
     }
   }
   __syncthreads();
@@ -329,13 +350,13 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     // ---- R phase: aggregate of tile t (from its stage; ragged tiles load directly)
     bool copy_lost = false;  // this thread's wait for the stage's bulk copy expired
     if (haveR) {
-      const TileRef rr = tile_ref<T, REV, EXT>(P, t);
-      T x[SCH][V], wx[SCH];
+      const TileRef rr = tile_ref<T, REV, EXT, CH>(P, t);
+      T x[CH][V], wx[CH];
       if (rr.full) {
         copy_lost = !mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u, kCopyWaitPolls, P.status);
-        const char* st = s_stage + sidx * kTileBytes;
+        const char* st = s_stage + sidx * TB;
 #pragma unroll
-        for (int c = 0; c < SCH; ++c) {
+        for (int c = 0; c < CH; ++c) {
           V16<T> va;
           const char* sp = st + (c * ST + tid) * 16;
           if (chk(sidx >= 0 && sidx < NST && ((uintptr_t)sp & 15) == 0, 103, P.status))
@@ -351,22 +372,22 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
           if constexpr (KIND != 0) ve.template eval_all<V>(&x[c][0], y);
         }
       } else {
-        V16<T> na[SCH], nb[SCH];
-        tile_values<T, KIND>(rr, two, tid, ve, ident, na, nb, x);
+        V16<T> na[CH], nb[CH];
+        tile_values<T, KIND, CH>(rr, two, tid, ve, ident, na, nb, x);
       }
       if constexpr (KEEP) {
         // the view's values stay in the stage (each thread its own chunks) for the
         // tile's S phase in the next iteration
-        char* st = s_stage + sidx * kTileBytes;
+        char* st = s_stage + sidx * TB;
 #pragma unroll
-        for (int c = 0; c < SCH; ++c) {
+        for (int c = 0; c < CH; ++c) {
           V16<T> v;
 #pragma unroll
           for (int e = 0; e < V; ++e) v.v[e] = x[c][e];
           *reinterpret_cast<V16<T>*>(st + (c * ST + tid) * 16) = v;
         }
       }
-      tile_reduce<T, OP>(x, s_totR, lane, warp);
+      tile_reduce<T, OP, CH>(x, s_totR, lane, warp);
     }
     // the ticket after the staged ones (needed only at the end of the iteration)
     const long long tlast = tk[kStages - 1];
@@ -402,47 +423,47 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     // ---- S phase: tile tprev again -- re-read from L2, or (a zip view) its view
     // values from the stage the R phase left them in -- scanned with its carry, stored
     if (haveS) {
-      const TileRef rs = tile_ref<T, REV, EXT>(P, tprev);
-      T x[SCH][V], wexc[SCH];
+      const TileRef rs = tile_ref<T, REV, EXT, CH>(P, tprev);
+      T x[CH][V], wexc[CH];
       if constexpr (KEEP) {
-        const char* st = s_stage + ((sidx + NST - 1) % NST) * kTileBytes;
+        const char* st = s_stage + ((sidx + NST - 1) % NST) * TB;
 #pragma unroll
-        for (int c = 0; c < SCH; ++c) {
+        for (int c = 0; c < CH; ++c) {
           const V16<T> v = *reinterpret_cast<const V16<T>*>(st + (c * ST + tid) * 16);
 #pragma unroll
           for (int e = 0; e < V; ++e) x[c][e] = v.v[e];
         }
         fence_proxy_async_smem();  // generic writes above precede the stage's next bulk copy
       } else {
-        V16<T> sa[SCH], sb[SCH];
-        if (rs.full) load_full<T>(rs, two, tid, drop, sa, sb, P.status);
-        tile_values<T, KIND>(rs, two, tid, ve, ident, sa, sb, x);
+        V16<T> sa[CH], sb[CH];
+        if (rs.full) load_full<T, CH>(rs, two, tid, drop, sa, sb, P.status);
+        tile_values<T, KIND, CH>(rs, two, tid, ve, ident, sa, sb, x);
       }
-      local_scan<T, OP, REV>(x, wexc, s_totS, lane, warp, ident);
+      local_scan<T, OP, REV, CH>(x, wexc, s_totS, lane, warp, ident);
       if (tid == 0) s_tk[kStages + (it & 1)] = tnew;  // the next ticket, published by this barrier
       __syncthreads();
-      // every warp scans the SQ chunk totals itself (no second barrier for a table
+      // every warp scans the Q chunk totals itself (no second barrier for a table
       // of offsets): the carry-in of each of this thread's chunks' warp segments
-      T cbase[SCH];
+      T cbase[CH];
       {
-        T loc[SR], exc, offs[SR];
-        block_totals<T, OP>(s_totS, lane, loc, exc);
+        T loc[R], exc, offs[R];
+        block_totals<T, OP, CH>(s_totS, lane, loc, exc);
         if (lane == 0) exc = ident;
         offs[0] = O::apply(s_pref, exc);
 #pragma unroll
-        for (int r = 1; r < SR; ++r) offs[r] = O::apply(offs[r - 1], loc[r - 1]);
+        for (int r = 1; r < R; ++r) offs[r] = O::apply(offs[r - 1], loc[r - 1]);
 #pragma unroll
-        for (int c = 0; c < SCH; ++c) {
-          const int q = REV ? SQ - 1 - (c * SNW + warp) : c * SNW + warp;
+        for (int c = 0; c < CH; ++c) {
+          const int q = REV ? Q - 1 - (c * SNW + warp) : c * SNW + warp;
           T sel = offs[0];
 #pragma unroll
-          for (int r = 1; r < SR; ++r)
-            if (q % SR == r) sel = offs[r];
-          cbase[c] = __shfl_sync(0xffffffffu, sel, q / SR);
+          for (int r = 1; r < R; ++r)
+            if (q % R == r) sel = offs[r];
+          cbase[c] = __shfl_sync(0xffffffffu, sel, q / R);
         }
       }
 #pragma unroll
-      for (int c = 0; c < SCH; ++c) {
+      for (int c = 0; c < CH; ++c) {
         const T pre = O::apply(cbase[c], wexc[c]);
         T y[V];
 #pragma unroll
@@ -483,7 +504,7 @@ __global__ void __launch_bounds__(ST, KIND == 3 ? 2 : kMinBlocks) k_scan(const _
     const int fill = (sidx + kStages) % NST;
     if (tid == 0) {
       fence_proxy_async_smem();
-      stage_issue<T, REV, EXT>(P, tn, s_stage + fill * kTileBytes, &s_bar[fill], two);
+      stage_issue<T, REV, EXT, CH>(P, tn, s_stage + fill * TB, &s_bar[fill], two);
     }
     parity ^= 1u << sidx;
     pend = (pend & ~(1u << sidx)) | (1u << fill);
@@ -548,7 +569,7 @@ __global__ void __launch_bounds__(ST) k_scan_wave(const __grid_constant__ ScanPa
     if (r.full) load_full<T>(r, false, tid, l2_policy_evict_first(), xa, xb, P.status);
     T x[SCH][V], wexc[SCH];
     ViewEval<T> ve;
-    tile_values<T, 0>(r, false, tid, ve, ident, xa, xb, x);
+    tile_values<T, 0, SCH>(r, false, tid, ve, ident, xa, xb, x);
     local_scan<T, OP, false>(x, wexc, s_tot, lane, warp, ident);
     __syncthreads();
     // every warp scans the chunk totals (the same order in each); thread 0

@@ -35,10 +35,11 @@ def _dt_code(dtype) -> int:
             torch.int32: L.DR_I32}[dtype]
 
 
-def scan_tile(dtype=torch.float32) -> int:
-    """Elements per tile of the scan kernel (the unit of its carry chain)."""
+def scan_tile(dtype=torch.float32, view=False) -> int:
+    """Elements per tile of the scan kernel (the unit of its carry chain); view:
+    the kernel for a fused view (ops or a zip)."""
     from paper_2406_00158_gb300 import _lib as L
-    return L.kernel_geometry(L.DR_K_SCAN, _dt_code(dtype))[0]
+    return L.kernel_geometry(L.DR_K_SCAN_VIEW if view else L.DR_K_SCAN, _dt_code(dtype))[0]
 
 
 def reduce_geometry(dtype=torch.float32):

@@ -144,6 +144,39 @@ def test_scan_flat_ragged_segments_repeated(ag):
                               oracle.reverse_inclusive_scan_f64(wi.astype(np.float64)).astype(np.float32))
 
 
+def test_scan_flat_fwd_bwd_captured_in_a_cuda_graph(ag):
+    """Forward and backward of the one-tensor scan captured into one CUDA graph
+    (no host work per step) and replayed on new data copied into the static
+    input and gradient: every replay bit-exact against the oracle."""
+    n = 8 * (3 * 8192 + 100)
+    lens = [n // 8] * 8
+    x = torch.zeros(n, device="cuda", requires_grad=True)
+    g = torch.zeros(n, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):          # warm-up: plans, workspaces, allocations
+        for _ in range(3):
+            x.grad = None
+            ag.inclusive_scan_flat(x, lens).backward(g)
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    x.grad = None
+    with torch.cuda.graph(graph):
+        y = ag.inclusive_scan_flat(x, lens)
+        y.backward(g)
+    for seed in range(2):
+        xi = inputs.uniform_int64(inputs.SEED_GRAD + 60 + seed, n, -1, 2)
+        wi = inputs.uniform_int64(inputs.SEED_GRAD + 70 + seed, n, -1, 2)
+        with torch.no_grad():
+            x.copy_(torch.from_numpy(xi.astype(np.float32)))
+            g.copy_(torch.from_numpy(wi.astype(np.float32)))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(y.detach().cpu().numpy(), oracle.inclusive_scan_i64(xi).astype(np.float32))
+        assert np.array_equal(x.grad.cpu().numpy(),
+                              oracle.reverse_inclusive_scan_f64(wi.astype(np.float64)).astype(np.float32))
+
+
 @pytest.mark.parametrize("n,lx,ly", [(300, [100, 200], [300]), (1 << 22, None, None)])
 def test_dot_grad(ag, n, lx, ly):
     x = inputs.uniform_pm1_f32(51, n)

@@ -241,6 +241,50 @@ def test_scan_over_fused_zip_transform(api):
     assert np.array_equal(G.to_np(out), oracle.inclusive_scan_i64(x * y))
 
 
+@pytest.mark.parametrize("n", [3 * 4096 + 77, 1 << 26])
+def test_scan_over_zip_view_exact_integer_valued(api, n):
+    """scan(zip(x, y) | multiply) in fp32 with x, y in {-1, 0, 1}: every product is
+    exact and every partial sum a range sum of a walk whose prefixes span less than
+    2^24 (checked), so the result must equal the oracle's integer scan bit for bit.
+    The operands are cut differently (8 equal segments against 1:2:3:2), so the
+    zip is re-segmented and tiles break at every union boundary; at 2^26 every
+    CTA of the zip kernel runs many tiles (the kept-stage pipeline in steady
+    state).  The reverse scan of the same view as well."""
+    xi = inputs.uniform_int64(inputs.SEED_DOT_X + 91, n, -1, 2)
+    yi = inputs.uniform_int64(inputs.SEED_DOT_Y + 91, n, -1, 2)
+    prod = xi * yi
+    fwd = oracle.inclusive_scan_i64(prod)
+    assert max(int(fwd.max()), 0) - min(int(fwd.min()), 0) < (1 << 24)
+    lx, ly = inputs.block_segments(n, 8), inputs.proportional_segments(n, [1, 2, 3, 2])
+    view = api.dot_view(G.segvec(xi.astype(np.float32), lx), G.segvec(yi.astype(np.float32), ly))
+    out = G.empty_like_vec([n // 2, n - n // 2], torch.float32)
+    api.inclusive_scan(view, out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), fwd.astype(np.float32))
+    api.reverse_inclusive_scan(view, out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), oracle.reverse_inclusive_scan_f64(prod.astype(np.float64)).astype(np.float32))
+
+
+@pytest.mark.parametrize("n", [3 * 4096 + 77, 1 << 26])
+def test_scan_over_one_leaf_view_exact_integer_valued(api, n):
+    """scan(x | scale(-1) | add(0)) in fp32 with x in {-1, 0, 1} (the fused
+    one-leaf view kernel, kept view values, 16 KB tiles): exact integer walk,
+    bit-exact against the oracle, forward and reverse, over 1:2:3:2 segments."""
+    xi = inputs.uniform_int64(inputs.SEED_DOT_X + 93, n, -1, 2)
+    fwd = oracle.inclusive_scan_i64(-xi)
+    assert max(int(fwd.max()), 0) - min(int(fwd.min()), 0) < (1 << 24)
+    lens = inputs.proportional_segments(n, [1, 2, 3, 2])
+    view = G.segvec(xi.astype(np.float32), lens).view().transform("scale", -1.0).transform("add", 0.0)
+    out = G.empty_like_vec(lens, torch.float32)
+    api.inclusive_scan(view, out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), fwd.astype(np.float32))
+    api.reverse_inclusive_scan(view, out)
+    api.sync_status()
+    assert np.array_equal(G.to_np(out), oracle.reverse_inclusive_scan_f64(-xi.astype(np.float64)).astype(np.float32))
+
+
 def test_reverse_scan(api):
     n = 123_457
     g = inputs.uniform_pm1_f32(73, n)
@@ -324,7 +368,7 @@ def test_scan_over_zip_view_float_within_bound(api):
     ref = oracle.inclusive_scan_f64(prod)
     absref = oracle.inclusive_scan_f64(np.abs(prod))
     pieces = [4000, n // 3 - 4000, n - n // 3]
-    tiles = G.tile_index(pieces, G.scan_tile(torch.float32))
+    tiles = G.tile_index(pieces, G.scan_tile(torch.float32, view=True))
     # each product is rounded once to fp32 before the scan: one more rounding per term
     bound = T.scan_bound(absref, tiles) + 2.0 ** -24 * absref
     assert np.all(np.abs(G.to_np(out).astype(np.float64) - ref) <= bound)
