@@ -94,7 +94,7 @@ typedef struct dr_piece {
 
 /* Launch shape of the batched kernel (chosen by the autotuner or the caller).
  * variant 0: one tile per CTA in registers; threads 128, 256 or 512; items 8 or 16.
- * variant 1: lookahead pipeline with TMA-staged x and p; threads 256; items 16 or 32. */
+ * variant 1: lookahead pipeline with TMA-staged x and p; threads 256; items 12, 16 or 32. */
 typedef struct dr_tune {
   int32_t threads;      /* threads per CTA */
   int32_t items;        /* elements per thread per tile (fp32) */

@@ -420,7 +420,7 @@ extern "C" int dr_batch_autotune(dr_batch* b, int mode, const char* cache_path, 
   double best_us = 1e30;
   // {variant, threads, items, max CTAs per SM}
   const int shapes[][4] = {{0, 128, 16, 8}, {0, 256, 8, 8}, {0, 256, 16, 8}, {0, 512, 8, 4},
-                           {0, 512, 16, 4}, {1, 256, 16, 3}, {1, 256, 32, 1}};
+                           {0, 512, 16, 4}, {1, 256, 12, 4}, {1, 256, 16, 3}, {1, 256, 32, 1}};
   const int ctas[] = {1, 2, 3, 4, 8};
   int rc = DR_OK, timed = 0;
   std::string last_msg;

@@ -322,10 +322,17 @@ __device__ __forceinline__ void la_reduce(const float (&x)[CH][4], float* s_tot,
   float c[CH];
 #pragma unroll
   for (int q = 0; q < CH; ++q) c[q] = fadd(fadd(x[q][0], x[q][1]), fadd(x[q][2], x[q][3]));
+  if constexpr ((CH & (CH - 1)) == 0) {
 #pragma unroll
-  for (int w = CH / 2; w >= 1; w >>= 1)
+    for (int w = CH / 2; w >= 1; w >>= 1)
 #pragma unroll
-    for (int q = 0; q < w; ++q) c[q] = fadd(c[q], c[q + w]);
+      for (int q = 0; q < w; ++q) c[q] = fadd(c[q], c[q + w]);
+  } else {  // pairwise over any count
+#pragma unroll
+    for (int w = 1; w < CH; w <<= 1)
+#pragma unroll
+      for (int q = 0; q + w < CH; q += 2 * w) c[q] = fadd(c[q], c[q + w]);
+  }
   const float s = warp_reduce<float, DR_PLUS>(c[0]);
   if (lane == 0) s_tot[warp] = s;
 }
@@ -580,7 +587,7 @@ cudaError_t go(const BatchParams& p, int ctas_per_sm, int sms, cudaStream_t s) {
 }  // namespace
 
 bool batch_shape_supported(int variant, int threads, int items) {
-  if (variant == 1) return threads == LT && (items == 16 || items == 32);
+  if (variant == 1) return threads == LT && (items == 12 || items == 16 || items == 32);
   return variant == 0 && (threads == 128 || threads == 256 || threads == 512) && (items == 8 || items == 16);
 }
 
@@ -593,6 +600,7 @@ cudaError_t launch_batch(const BatchParams& p, const dr_tune& t, int sms, cudaSt
   if (p.ntiles <= 0) return cudaSuccess;
   const int ch = t.items / 4;
   if (t.variant == 1) {
+    if (ch == 3) return go_la<3, 4>(p, t.ctas_per_sm, sms, s);
     if (ch == 4) return go_la<4, 3>(p, t.ctas_per_sm, sms, s);
     if (ch == 8) return go_la<8, 1>(p, t.ctas_per_sm, sms, s);
     return cudaErrorInvalidValue;

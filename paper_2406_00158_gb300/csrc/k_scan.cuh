@@ -58,22 +58,20 @@ constexpr int ST = DR_SCAN_THREADS;  // threads per CTA
 constexpr int SCH = DR_SCAN_CHUNKS;  // 16-byte chunks per thread per tile (8: 32 KB tiles)
 constexpr int SNW = ST / 32;      // warps
 constexpr int SQ = SCH * SNW;     // warp-chunk totals per tile
-constexpr int SR = SQ / 32;       // totals per lane of warp 0
+constexpr int SR = (SQ + 31) / 32;  // totals per lane in the block scan
 constexpr int kLookbackG = DR_SCAN_LOOKBACK_G;  // lookback slots per lane per round
 constexpr int kMinBlocks = DR_SCAN_MINB;        // resident CTAs per SM
 constexpr int kStages = 2;        // tiles ticketed ahead: the tile being reduced + the next
 constexpr int kTileBytes = ST * SCH * 16;
 constexpr int kViewChunks = DR_SCAN_VIEW_CHUNKS;  // chunks per thread of a fused view's tile
 constexpr int kViewMinBlocks = 4;                 // resident CTAs per SM of the fused-view kernels
-static_assert(SQ % 32 == 0, "block-level scan assumes a multiple of 32 totals");
 
 // Tile geometry for CH 16-byte chunks per thread.
 template <int CH>
 struct Geo {
   static constexpr int SQ = CH * SNW;        // warp-chunk totals per tile
-  static constexpr int SR = SQ / 32;         // totals per lane in the block scan
+  static constexpr int SR = (SQ + 31) / 32;  // totals per lane in the block scan
   static constexpr int TB = ST * CH * 16;    // tile bytes
-  static_assert(SQ % 32 == 0, "block-level scan assumes a multiple of 32 totals");
 };
 
 // A fused view (KIND 2, 3) keeps the view's values of a reduced tile in its
@@ -238,10 +236,17 @@ __device__ __forceinline__ void tile_reduce(const T (&x)[CH][16 / sizeof(T)], T*
     for (int e = 1; e < V; ++e) a = O::apply(a, x[q][e]);
     c[q] = a;
   }
+  if constexpr ((CH & (CH - 1)) == 0) {
 #pragma unroll
-  for (int w = CH / 2; w >= 1; w >>= 1)
+    for (int w = CH / 2; w >= 1; w >>= 1)
 #pragma unroll
-    for (int q = 0; q < w; ++q) c[q] = O::apply(c[q], c[q + w]);
+      for (int q = 0; q < w; ++q) c[q] = O::apply(c[q], c[q + w]);
+  } else {  // pairwise over any count
+#pragma unroll
+    for (int w = 1; w < CH; w <<= 1)
+#pragma unroll
+      for (int q = 0; q + w < CH; q += 2 * w) c[q] = O::apply(c[q], c[q + w]);
+  }
   const T s = warp_reduce<T, OP>(c[0]);
   if (lane == 0) s_tot[warp] = s;
 }
@@ -251,12 +256,14 @@ __device__ __forceinline__ void tile_reduce(const T (&x)[CH][16 / sizeof(T)], T*
 template <typename T, int OP, int CH = SCH>
 __device__ __forceinline__ T block_totals(const T* s_tot, int lane, T (&loc)[Geo<CH>::SR], T& exc) {
   using O = Op<OP>;
-  constexpr int R = Geo<CH>::SR;
-  T lsum = s_tot[lane * R];
+  constexpr int R = Geo<CH>::SR, Q = Geo<CH>::SQ;
+  const T ident = O::template identity<T>();
+  // lanes past the Q totals (when Q is not a multiple of 32) contribute the identity
+  T lsum = (Q % 32 == 0 || lane * R < Q) ? s_tot[lane * R] : ident;
   loc[0] = lsum;
 #pragma unroll
   for (int r = 1; r < R; ++r) {
-    loc[r] = s_tot[lane * R + r];
+    loc[r] = (Q % 32 == 0 || lane * R + r < Q) ? s_tot[lane * R + r] : ident;
     lsum = O::apply(lsum, loc[r]);
   }
   const T inc = warp_inclusive<T, OP, false>(lsum, lane);

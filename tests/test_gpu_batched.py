@@ -55,7 +55,7 @@ def small_shapes():
 
 
 @pytest.mark.parametrize("tune", [None, (128, 16, 4, 0), (256, 8, 2, 0), (512, 16, 1, 0), (256, 16, 3, 1),
-                                  (256, 32, 1, 1), (256, 16, 1, 1)])
+                                  (256, 32, 1, 1), (256, 16, 1, 1), (256, 12, 4, 1)])
 def test_batch_small_vs_oracle_repeat_graph_per_range(api, tune):
     shapes = small_shapes()
     x, p, xs, ps, ys, dots = build(api, shapes)
