@@ -64,7 +64,10 @@ constexpr int kMinBlocks = DR_SCAN_MINB;        // resident CTAs per SM
 constexpr int kStages = 2;        // tiles ticketed ahead: the tile being reduced + the next
 constexpr int kTileBytes = ST * SCH * 16;
 constexpr int kViewChunks = DR_SCAN_VIEW_CHUNKS;  // chunks per thread of a fused view's tile
-constexpr int kViewMinBlocks = 4;                 // resident CTAs per SM of the fused-view kernels
+#ifndef DR_SCAN_VIEW_MINB
+#define DR_SCAN_VIEW_MINB 4
+#endif
+constexpr int kViewMinBlocks = DR_SCAN_VIEW_MINB;  // resident CTAs per SM of the fused-view kernels
 
 // Tile geometry for CH 16-byte chunks per thread.
 template <int CH>
