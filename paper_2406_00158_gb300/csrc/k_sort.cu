@@ -34,9 +34,6 @@ namespace {
 #ifndef DR_SORT_ITEMS
 #define DR_SORT_ITEMS 16
 #endif
-#ifndef DR_SORT_CHAINS
-#define DR_SORT_CHAINS 1  // independent counter chains per warp in the rank (1 or 2)
-#endif
 #ifndef DR_SORT_MINB
 #define DR_SORT_MINB 4  // resident CTAs per SM the scatter is compiled for (0: no bound)
 #endif
@@ -152,8 +149,10 @@ __device__ __forceinline__ T view_elem(const KPiece& pc, int64_t j, const ViewEv
 // issue slots, bounds the ranking).  Shapes: 256 x 16 and 512 x 12 tie; 1024
 // threads and 24 items per thread are slower.  The scatter compiled for 4 CTAs per
 // SM (64 registers) beats 3 (78 registers) by 2 %; 12 or 8 items per thread at 4 or
-// 6 CTAs per SM are slower (6.17, 6.91 ms against 5.98 ms for 2^28 fp32 keys), and
-// match.any at 4 CTAs per SM takes 7.6 ms.
+// 6 CTAs per SM are slower (6.17, 6.91 ms against 5.98 ms for 2^28 fp32 keys),
+// match.any at 4 CTAs per SM takes 7.6 ms, and two interleaved counter chains per
+// warp (half the items each, the second half adding the first half's counts)
+// 6.21 ms: the rank is bound by instruction issue, not by the chain's latency.
 #ifndef DR_SORT_MATCH
 #define DR_SORT_MATCH 0
 #endif
@@ -225,8 +224,7 @@ __device__ __forceinline__ int load_tile(const SortParams& P, int64_t tile, type
 // the running per-digit counts of the warp (hist: its row of the CTA's table,
 // zeroed), kept by each group's leader.  FULL: every lane holds a key.
 template <typename K, bool FULL>
-__device__ __forceinline__ void rank_warp(const K* key, int shift, int cnt, unsigned* hist, unsigned* hist2,
-                                          unsigned* rank) {
+__device__ __forceinline__ void rank_warp(const K* key, int shift, int cnt, unsigned* hist, unsigned* rank) {
   constexpr int SIT = Tile<sizeof(K)>::IT;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned peers[SIT];
@@ -238,44 +236,16 @@ __device__ __forceinline__ void rank_warp(const K* key, int shift, int cnt, unsi
     peers[i] = same_digit_lanes<FULL ? 8 : 9>(dig[i]);
   }
   const unsigned lt = (1u << lane) - 1u;
-  if constexpr (DR_SORT_CHAINS == 1) {
 #pragma unroll
-    for (int i = 0; i < SIT; ++i) {
-      const int leader = __ffs(peers[i]) - 1;
-      unsigned old = 0;
-      if (lane == leader && (FULL || dig[i] < RADIX)) {
-        old = hist[dig[i]];
-        hist[dig[i]] = old + __popc(peers[i]);
-      }
-      old = __shfl_sync(0xffffffffu, old, leader);
-      rank[i] = old + __popc(peers[i] & lt);
-      __syncwarp();
+  for (int i = 0; i < SIT; ++i) {
+    const int leader = __ffs(peers[i]) - 1;
+    unsigned old = 0;
+    if (lane == leader && (FULL || dig[i] < RADIX)) {
+      old = hist[dig[i]];
+      hist[dig[i]] = old + __popc(peers[i]);
     }
-  } else {
-    // two independent chains: items [0, SIT/2) count in hist, [SIT/2, SIT) in hist2
-    // (interleaved, so each chain's shared-memory latency hides the other's); the
-    // second half then adds the first half's final counts of its digit
-    constexpr int H = SIT / 2;
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = i + h * H;
-        unsigned* hh = h ? hist2 : hist;
-        const int leader = __ffs(peers[j]) - 1;
-        unsigned old = 0;
-        if (lane == leader && (FULL || dig[j] < RADIX)) {
-          old = hh[dig[j]];
-          hh[dig[j]] = old + __popc(peers[j]);
-        }
-        old = __shfl_sync(0xffffffffu, old, leader);
-        rank[j] = old + __popc(peers[j] & lt);
-      }
-      __syncwarp();
-    }
-#pragma unroll
-    for (int j = H; j < SIT; ++j)
-      if (FULL || dig[j] < RADIX) rank[j] += hist[dig[j]];
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rank[i] = old + __popc(peers[i] & lt);
     __syncwarp();
   }
 }
@@ -314,7 +284,6 @@ __global__ void DR_SORT_SCATTER_BOUNDS k_sort_scatter(const __grid_constant__ So
   constexpr int SIT = Tile<sizeof(K)>::IT, STILE = Tile<sizeof(K)>::N;
   __shared__ K skeys[STILE];
   __shared__ unsigned whist[SW][RADIX];
-  __shared__ unsigned whist2[DR_SORT_CHAINS == 2 ? SW : 1][RADIX];
   __shared__ unsigned dstart[RADIX];
   __shared__ int dshift[RADIX];  // global start of digit d here minus its tile start
   __shared__ unsigned wsum[SW];
@@ -328,8 +297,6 @@ __global__ void DR_SORT_SCATTER_BOUNDS k_sort_scatter(const __grid_constant__ So
   const int shift = 8 * P.pass;
   const int64_t tile = blockIdx.x;
   for (int i = tid; i < SW * RADIX; i += ST) (&whist[0][0])[i] = 0;
-  if constexpr (DR_SORT_CHAINS == 2)
-    for (int i = tid; i < SW * RADIX; i += ST) (&whist2[0][0])[i] = 0;
   if constexpr (DST == 1)
     for (int i = tid; i < P.npout; i += ST) ostart[i] = P.out[i].start;
   // scanned counts: global position of the tile's first key of digit tid (< 2^30)
@@ -338,9 +305,8 @@ __global__ void DR_SORT_SCATTER_BOUNDS k_sort_scatter(const __grid_constant__ So
   const int cnt = load_tile<T, SRC>(P, tile, key);
   __syncthreads();
   unsigned rank[SIT];
-  unsigned* h2 = DR_SORT_CHAINS == 2 ? &whist2[DR_SORT_CHAINS == 2 ? w : 0][0] : nullptr;
-  if (cnt == STILE) rank_warp<K, true>(key, shift, cnt, &whist[w][0], h2, rank);
-  else rank_warp<K, false>(key, shift, cnt, &whist[w][0], h2, rank);
+  if (cnt == STILE) rank_warp<K, true>(key, shift, cnt, &whist[w][0], rank);
+  else rank_warp<K, false>(key, shift, cnt, &whist[w][0], rank);
   __syncthreads();
 
   // thread d: digit d's exclusive prefix over warps and the tile's count of d;
@@ -350,7 +316,7 @@ __global__ void DR_SORT_SCATTER_BOUNDS k_sort_scatter(const __grid_constant__ So
   if (d < RADIX) {
 #pragma unroll
     for (int k = 0; k < SW; ++k) {
-      const unsigned c = whist[k][d] + (DR_SORT_CHAINS == 2 ? whist2[DR_SORT_CHAINS == 2 ? k : 0][d] : 0u);
+      const unsigned c = whist[k][d];
       whist[k][d] = tot;
       tot += c;
     }
