@@ -295,8 +295,23 @@ def measure_rows(api, dev, s, peak) -> dict:
         v = vx.view()
         fn = lambda: api.inclusive_scan(v, vo, stream=s)
         if n < (1 << 24):
+            # kernel time without the host's per-call launch cost: 20 back-to-back calls
+            # captured into one CUDA graph, replayed (L2-resident)
+            side = torch.cuda.Stream()
+            side.wait_stream(s)
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    api.inclusive_scan(v, vo, stream=side)
+            s.wait_stream(side)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                for _ in range(20):
+                    api.inclusive_scan(v, vo)
+            ms_graph = _time(g.replay, s, 20) / 20
             rows[name] = _row(_time(fn, s, 50, flush), n * 16, peak, l2="flushed between calls",
-                              l2_resident=_row(_time(fn, s, 200), n * 16, peak))
+                              l2_resident=_row(_time(fn, s, 200), n * 16, peak),
+                              graph_replay=_row(ms_graph, n * 16, peak, note="20 calls per graph, L2-resident"))
+            del g
         else:
             rows[name] = _row(_time(fn, s, 20), n * 16, peak, l2="4 GiB per array > L2")
         api.sync_status(s)

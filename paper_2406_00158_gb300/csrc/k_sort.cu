@@ -251,7 +251,8 @@ __device__ __forceinline__ void rank_warp(const K* key, int shift, int cnt, unsi
 }
 
 // ---------------------------------------------------------------------------
-// 1. Per-tile digit counts, digit-major.
+// 1. Per-tile digit counts, digit-major.  (Counting 4 tiles per CTA, or into one
+// histogram per warp, measured no faster: 5.99 / 6.10 ms against 5.99 ms per sort.)
 // ---------------------------------------------------------------------------
 template <typename T, int SRC>
 __global__ void __launch_bounds__(ST) k_sort_count(const __grid_constant__ SortParams P) {
