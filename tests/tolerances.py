@@ -54,9 +54,18 @@ def reduce_bound(n: int, abs_sum: float, sms: int, esize: int) -> float:
 
 
 def scan_bound(abs_prefix, tile_of_elem):
-    """Per-element bound |y_i - y*_i| <= gamma(6 T_i + 20) * S_i, T_i = 1 + tile index."""
+    """Per-element bound |y_i - y*_i| <= gamma(7 T_i + 20) * S_i, T_i = 1 + tile index,
+    S_i the prefix of |x|: the longest chain of dependent fp32 roundings any input
+    passes through on its way to y_i, counted for the scan kernels.  Inside a tile:
+    thread scan (<= 3), warp scan (5), the block scan of the chunk totals (<= 7),
+    the carry-in and the element's own add (2): <= 20.  An input of an earlier tile:
+    its tile's aggregate (a reduction tree: thread 3, chunk tree <= 3, warp 5, block
+    5 = 16), then per lookback hop the 5-level warp reduction of the window, the
+    combine with the running carry and the published inclusive prefix (7), at most
+    one hop per tile, and 4 roundings carrying the prefix into the output:
+    16 + 1 + 7 (T - 1) + 4 <= 7 T + 20."""
     import numpy as np
-    k = 6.0 * (np.asarray(tile_of_elem, dtype=np.float64) + 1.0) + 20.0
+    k = 7.0 * (np.asarray(tile_of_elem, dtype=np.float64) + 1.0) + 20.0
     return k * U32 / (1.0 - k * U32) * np.asarray(abs_prefix)
 
 
