@@ -1,4 +1,4 @@
-"""The sharded path (one range over N ranks, SURVEY-style segments -> ranks) on
+"""The sharded path (one range over N ranks, its segments placed on the ranks) on
 CPU gloo ranks, world sizes 2 and 3: the placement and exchange logic of
 paper_2406_00158_gb300.shard -- all-gather of partials and run totals, carries,
 point-to-point halo rows -- with a CPU stand-in for the local kernels, checked
