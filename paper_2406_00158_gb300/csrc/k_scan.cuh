@@ -5,8 +5,9 @@
 // scans them, and makes a second pass that adds each segment's offset: four
 // accesses per element (Sec. 5, "Inclusive Scan" blames that second pass for
 // the 1 -> 2 tile drop).  Here all segments are pieces of one global tile
-// order (32 KB tiles, cut per piece) and the carry crosses segment boundaries
-// inside one pass: decoupled lookback, two HBM accesses per element.
+// order (32 KB tiles, 16 KB for fused views, cut per piece) and the carry
+// crosses segment boundaries inside one pass: decoupled lookback, two HBM
+// accesses per element.
 //
 // Lookahead pipeline (persistent CTAs, tiles handed out by an atomic ticket).
 // Iteration k of a CTA handles two tiles:
