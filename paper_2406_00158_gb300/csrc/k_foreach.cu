@@ -191,14 +191,16 @@ __device__ __forceinline__ int find_tile_piece(const PC* pc, int n, int64_t tile
   return lo;
 }
 
-// The inline table (kernel parameters) or the device table, searched in separate
-// branches so that each keeps its address space.
-template <typename T, int FN>
-__device__ __forceinline__ int find_fe_piece(const ForEachParams& P, int64_t tile) {
-  return P.pc_ext ? find_tile_piece(P.pc_ext, P.npieces, tile) : find_tile_piece(P.pc, P.npieces, tile);
+// The piece table: inline in the kernel parameters (read through the constant
+// cache), or, with EXT, in device memory (more pieces than the parameters hold).
+// A compile-time choice, so that every piece access keeps its address space.
+template <bool EXT, typename PP>
+__device__ __forceinline__ const auto* fe_table(const PP& P) {
+  if constexpr (EXT) return P.pc_ext;
+  else return P.pc;
 }
 
-template <typename T, int FN>
+template <typename T, int FN, bool EXT>
 __global__ void __launch_bounds__(FT) k_for_each(const __grid_constant__ ForEachParams P) {
   using F = Fn<T, FN>;
   constexpr int VN = 16 / sizeof(T);
@@ -208,8 +210,9 @@ __global__ void __launch_bounds__(FT) k_for_each(const __grid_constant__ ForEach
   const unsigned long long pol = l2_policy_evict_first();
   const int tid = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
-    const int k = find_fe_piece<T, FN>(P, tile);
-    const FePiece& pc = P.pc_ext ? P.pc_ext[k] : P.pc[k];
+    const auto* tab = fe_table<EXT>(P);
+    const int k = find_tile_piece(tab, P.npieces, tile);
+    const FePiece& pc = tab[k];
     const int64_t base = (tile - pc.tile_begin) * TILE;
     if (!chk(k >= 0 && k < P.npieces && base >= 0 && base < pc.len, 400, P.status)) continue;
     if (pc.vec_ok && pc.len - base >= TILE) {
@@ -259,10 +262,6 @@ __global__ void __launch_bounds__(FT) k_for_each(const __grid_constant__ ForEach
 // ---------------------------------------------------------------------------
 // transform: out = view (KIND 0: one plain leaf; 1: a * b; 2: interpreted chain)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_tr_piece(const TransformParams& P, int64_t tile) {
-  return P.pc_ext ? find_tile_piece(P.pc_ext, P.npieces, tile) : find_tile_piece(P.pc, P.npieces, tile);
-}
-
 template <typename T, int KIND>
 __device__ __forceinline__ T tr_eval(const ViewEval<T>& ve, T a, T b) {
   if constexpr (KIND == 0) return a;
@@ -270,7 +269,7 @@ __device__ __forceinline__ T tr_eval(const ViewEval<T>& ve, T a, T b) {
   else return ve(a, b);
 }
 
-template <typename T, int KIND>
+template <typename T, int KIND, bool EXT>
 __global__ void __launch_bounds__(FT) k_transform(const __grid_constant__ TransformParams P) {
   constexpr int VN = 16 / sizeof(T);
   constexpr int TILE = ftile<T>();
@@ -280,8 +279,9 @@ __global__ void __launch_bounds__(FT) k_transform(const __grid_constant__ Transf
   const unsigned long long pol = l2_policy_evict_first();
   const int tid = threadIdx.x;
   for (int64_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
-    const int k = find_tr_piece(P, tile);
-    const KPiece& pc = P.pc_ext ? P.pc_ext[k] : P.pc[k];
+    const auto* tab = fe_table<EXT>(P);
+    const int k = find_tile_piece(tab, P.npieces, tile);
+    const KPiece& pc = tab[k];
     const int64_t base = (tile - pc.tile_begin) * TILE;
     if (!chk(k >= 0 && k < P.npieces && base >= 0 && base < pc.len, 410, P.status)) continue;
     if (pc.vec_ok && pc.len - base >= TILE) {
@@ -340,9 +340,14 @@ int resident_grid(OccCache& occ, K* kernel, int64_t ntiles) {
 
 template <typename T, int FN>
 cudaError_t run_fe(const ForEachParams& p, cudaStream_t s) {
-  static OccCache occ;
-  const int grid = resident_grid(occ, k_for_each<T, FN>, p.ntiles);
-  k_for_each<T, FN><<<grid, FT, 0, s>>>(p);
+  static OccCache occ, occx;
+  if (p.pc_ext) {
+    const int grid = resident_grid(occx, k_for_each<T, FN, true>, p.ntiles);
+    k_for_each<T, FN, true><<<grid, FT, 0, s>>>(p);
+  } else {
+    const int grid = resident_grid(occ, k_for_each<T, FN, false>, p.ntiles);
+    k_for_each<T, FN, false><<<grid, FT, 0, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
@@ -360,9 +365,14 @@ cudaError_t run_fe_t(const ForEachParams& p, cudaStream_t s) {
 
 template <typename T, int KIND>
 cudaError_t run_tr(const TransformParams& p, cudaStream_t s) {
-  static OccCache occ;
-  const int grid = resident_grid(occ, k_transform<T, KIND>, p.ntiles);
-  k_transform<T, KIND><<<grid, FT, 0, s>>>(p);
+  static OccCache occ, occx;
+  if (p.pc_ext) {
+    const int grid = resident_grid(occx, k_transform<T, KIND, true>, p.ntiles);
+    k_transform<T, KIND, true><<<grid, FT, 0, s>>>(p);
+  } else {
+    const int grid = resident_grid(occ, k_transform<T, KIND, false>, p.ntiles);
+    k_transform<T, KIND, false><<<grid, FT, 0, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
