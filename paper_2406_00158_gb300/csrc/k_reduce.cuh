@@ -58,7 +58,10 @@ __device__ __forceinline__ T block_reduce(T v, T* s_w) {
 }
 
 // KIND: 0 one leaf, no ops; 1 zip(a, b) | multiply, PLUS only; 2 generic view.
-template <typename T, int OP, int KIND>
+// EXT: the piece table is in device memory (more pieces than the kernel
+// parameters hold) -- a compile-time choice, so that every piece access keeps
+// its address space (the inline table is read through the constant cache).
+template <typename T, int OP, int KIND, bool EXT>
 __global__ void __launch_bounds__(RT, RCTAS) k_reduce(const __grid_constant__ ReduceParams P) {
   constexpr int V = 16 / sizeof(T);
   constexpr int TILE = rtile<T>();
@@ -76,10 +79,11 @@ __global__ void __launch_bounds__(RT, RCTAS) k_reduce(const __grid_constant__ Re
   for (int e = 0; e < V; ++e) acc[e] = O::template identity<T>();
 
   for (int64_t tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
-    // the inline table (kernel parameters) or the device table, searched in
-    // separate branches so that each keeps its address space
-    const int k = P.pc_ext ? find_piece(P.pc_ext, P.npieces, tile) : find_piece(P.pc, P.npieces, tile);
-    const KPiece& pc = P.pc_ext ? P.pc_ext[k] : P.pc[k];
+    const KPiece* tab;
+    if constexpr (EXT) tab = P.pc_ext;
+    else tab = P.pc;
+    const int k = find_piece(tab, P.npieces, tile);
+    const KPiece& pc = tab[k];
     const int64_t base = (tile - pc.tile_begin) * TILE;
     if (!chk(k >= 0 && k < P.npieces && base >= 0 && base < pc.len, 200, P.status)) continue;
     if (pc.vec_ok && pc.len - base >= TILE) {
@@ -165,7 +169,8 @@ __global__ void __launch_bounds__(RT, RCTAS) k_reduce(const __grid_constant__ Re
 template <typename T, int OP, int KIND>
 cudaError_t go(const ReduceParams& p, int grid, cudaStream_t s) {
   if (p.ntiles < grid) grid = (int)(p.ntiles > 0 ? p.ntiles : 1);
-  k_reduce<T, OP, KIND><<<grid, RT, 0, s>>>(p);
+  if (p.pc_ext) k_reduce<T, OP, KIND, true><<<grid, RT, 0, s>>>(p);
+  else k_reduce<T, OP, KIND, false><<<grid, RT, 0, s>>>(p);
   return cudaGetLastError();
 }
 
