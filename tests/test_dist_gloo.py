@@ -71,3 +71,27 @@ def test_reference_arm_prints_on_rank0_only():
     j = json.loads(lines[0][0])
     assert j["impl"] == "reference" and j["unit"] == "GB/s" and j["value"] > 0
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_all_cores_oracle_baseline_spawns_and_times_every_slice(tmp_path):
+    """bench.cpu_oracle_all_cores: spawned processes (no fork after any device
+    work), each timing the oracle on its own slice; the bytes are the whole
+    sample's and the wall time spans every process's run."""
+    code = r'''
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import bench
+from paper_2406_00158_gb300 import inputs
+if __name__ == "__main__":
+    n = 1 << 16
+    x = inputs.uniform_pm1_f32(inputs.SEED_DOT_X, n)
+    y = inputs.uniform_pm1_f32(inputs.SEED_DOT_Y, n)
+    dt, nb = bench.cpu_oracle_all_cores(x, y, 2, 3)
+    print(json.dumps({"dt": dt, "nb": nb, "expect": 2 * n * (bench.BYTES_DOT + bench.BYTES_SCAN)}))
+'''
+    path = tmp_path / "allcores_main.py"   # spawned children re-import the main script
+    path.write_text(code)
+    r = subprocess.run([sys.executable, str(path), ROOT], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["nb"] == out["expect"] and out["dt"] > 0
