@@ -5,7 +5,7 @@
 // scans them, and makes a second pass that adds each segment's offset: four
 // accesses per element (Sec. 5, "Inclusive Scan" blames that second pass for
 // the 1 -> 2 tile drop).  Here all segments are pieces of one global tile
-// order (32 KB tiles, 16 KB for fused views, cut per piece) and the carry
+// order (32 KB tiles, 12 KB for fused views, cut per piece) and the carry
 // crosses segment boundaries inside one pass: decoupled lookback, two HBM
 // accesses per element.
 //
@@ -53,7 +53,7 @@ namespace kscan {
 #define DR_SCAN_THREADS 256
 #endif
 #ifndef DR_SCAN_VIEW_CHUNKS
-#define DR_SCAN_VIEW_CHUNKS 4
+#define DR_SCAN_VIEW_CHUNKS 3
 #endif
 constexpr int ST = DR_SCAN_THREADS;  // threads per CTA
 constexpr int SCH = DR_SCAN_CHUNKS;  // 16-byte chunks per thread per tile (8: 32 KB tiles)
@@ -66,7 +66,7 @@ constexpr int kStages = 2;        // tiles ticketed ahead: the tile being reduce
 constexpr int kTileBytes = ST * SCH * 16;
 constexpr int kViewChunks = DR_SCAN_VIEW_CHUNKS;  // chunks per thread of a fused view's tile
 #ifndef DR_SCAN_VIEW_MINB
-#define DR_SCAN_VIEW_MINB 4
+#define DR_SCAN_VIEW_MINB 6
 #endif
 constexpr int kViewMinBlocks = DR_SCAN_VIEW_MINB;  // resident CTAs per SM of the fused-view kernels
 
@@ -81,10 +81,11 @@ struct Geo {
 // A fused view (KIND 2, 3) keeps the view's values of a reduced tile in its
 // stage until the tile's S phase, instead of re-reading its leaves from L2 and
 // evaluating the view again: one more stage (the tile being reduced, the next
-// one, and the one awaiting its S phase).  Its tiles are half as long (16 KB),
-// so the three stages (48 KB) let four CTAs share an SM (compiled for 64
-// registers; measured against three per SM: zip·mul scan of 2^28 fp32 0.720 ->
-// 0.600 ms, a one-leaf view 0.662 -> 0.552 ms).
+// one, and the one awaiting its S phase).  Its tiles are short (12 KB), so the
+// three stages (36 KB) let six CTAs share an SM (compiled for 40 registers).
+// Measured (2^28 fp32, zip·mul / one-leaf view): 16 KB tiles at 3 CTAs/SM 0.720 /
+// 0.662 ms, at 4 CTAs/SM 0.600 / 0.552 ms; 12 KB tiles at 5 CTAs/SM 0.640 /
+// 0.591 ms, at 6 CTAs/SM 0.580 / 0.548 ms.
 template <int KIND>
 __host__ __device__ constexpr int chunks() { return KIND != 0 ? kViewChunks : SCH; }
 template <int KIND>

@@ -440,13 +440,13 @@ def test_scale_by_partner_validation(lib):
 
 def test_kernel_geometry_host_only(lib):
     """Tile sizes the error bounds are derived from: 32 KB scan tiles (8192 fp32,
-    4096 int64), 16 KB tiles for the scan of a fused view, 16 KB reduce tiles
+    4096 int64), 12 KB tiles for the scan of a fused view, 16 KB reduce tiles
     with a fixed 4 CTAs per SM."""
     assert L.kernel_geometry(L.DR_K_SCAN, L.DR_F32) == (8192, 0)
     assert L.kernel_geometry(L.DR_K_SCAN, L.DR_I64) == (4096, 0)
     assert L.kernel_geometry(L.DR_K_SCAN, L.DR_I32) == (8192, 0)
-    assert L.kernel_geometry(L.DR_K_SCAN_VIEW, L.DR_F32) == (4096, 0)
-    assert L.kernel_geometry(L.DR_K_SCAN_VIEW, L.DR_I64) == (2048, 0)
+    assert L.kernel_geometry(L.DR_K_SCAN_VIEW, L.DR_F32) == (3072, 0)
+    assert L.kernel_geometry(L.DR_K_SCAN_VIEW, L.DR_I64) == (1536, 0)
     assert L.kernel_geometry(L.DR_K_REDUCE, L.DR_F32) == (4096, 4)
     assert L.kernel_geometry(L.DR_K_REDUCE, L.DR_F64) == (2048, 4)
     t, _ = L.kernel_geometry(L.DR_K_FOREACH, L.DR_F64)
