@@ -629,7 +629,8 @@ def main() -> None:
                     help="profiling helper: only run the stencil on an N x N grid (8 row blocks), 5 steps")
     ap.add_argument("--scan-only", default="", metavar="DTYPE",
                     help="profiling helper: only the inclusive scan of 2^log2n int64 (i64) or fp32 (f32) "
-                         "elements in 4 segments 1:2:3:2, 5 times")
+                         "elements in 4 segments 1:2:3:2, or of zip(x, y) | multiply (zip: fp32, 8 "
+                         "segments), 5 times")
     ap.add_argument("--batched-only", type=int, default=0, metavar="NVEC",
                     help="profiling helper: only the batched scan + dot over NVEC vectors of the batch "
                          "recipe, one launch, 5 times")
@@ -675,10 +676,18 @@ def main() -> None:
         vx = api.SegmentedVector.from_tensor(x, lens)
         vo = api.SegmentedVector.empty(lens, x.dtype, dev)
         v = vx.view()
+        nb = 2 * x.element_size() * n
+        if args.scan_only == "zip":  # the fused zip(x, y) | multiply view, 8 equal segments each
+            segs = [n // 8] * 8
+            vx = api.SegmentedVector.from_tensor(x, segs)
+            vy = api.SegmentedVector.from_tensor(
+                torch.from_numpy(inputs.uniform_pm1_f32(inputs.SEED_DOT_Y, n)).to(dev), segs)
+            vo = api.SegmentedVector.empty(segs, x.dtype, dev)
+            v = api.dot_view(vx, vy)
+            nb = 3 * x.element_size() * n
         s = torch.cuda.current_stream()
         ms = _time(lambda: api.inclusive_scan(v, vo, stream=s), s, 5)
         api.sync_status(s)
-        nb = 2 * x.element_size() * n
         print(json.dumps({"scan": args.scan_only, "n": n, "ms": ms, "GB/s": nb / (ms / 1e3) / 1e9}))
         return
     if args.batched_only:
